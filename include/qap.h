@@ -1,0 +1,215 @@
+/*
+ * qap.h - C-ABI of the GB300 swap-neighbourhood QAP search library.
+ *
+ * The library evaluates, selects and applies pairwise-exchange moves for the
+ * quadratic assignment problem, the inner loop shared by best-improvement
+ * 2opt and tabu search in Novoa & Qasem, "GPU-accelerated Parallel Solutions
+ * to the Quadratic Assignment Problem":
+ *
+ *   cost   Section 2.1, Eq. 1:  cost(p) = sum_i sum_j F[i][j] * D[p[i]][p[j]]
+ *   delta  Section 4.1, Eq. 2:  change of cost when units r < s exchange
+ *          locations (with the diagonal term the printed formula omits)
+ *   2opt   Section 4.1: move to the best neighbour until none improves
+ *   tabu   Sections 4.3-4.4: best admissible neighbour (not tabu, or
+ *          aspiring below the best cost), tabu tenure drawn from a range,
+ *          early stop when no move is admissible
+ *   walks  Sections 4.2, 4.4: many independent searches from random starts;
+ *          the caller takes the minimum over walks.
+ *
+ * Conventions
+ *   - p[u] is the location (0-based) of unit u.  The paper's pi (unit at a
+ *     location) is the inverse permutation; costs are identical.
+ *   - F and D are n x n, row-major.  F is the flow between units, D the
+ *     distance between locations.
+ *   - A move (r, s), r < s, swaps p[r] and p[s].  Ties between equal deltas
+ *     go to the lexicographically lowest (r, s).
+ *   - Walk k of a call draws its random numbers with Philox4x32-10 under
+ *     key = seed and counter (walk id, stream, draw / 4, 0), where walk id =
+ *     walk_base + k; stream 0 is the Fisher-Yates start permutation (draw
+ *     n-1-i picks j in [0, i] for position i, as (x * (i+1)) >> 32), stream 1
+ *     the tabu tenures (draw (it-1)/period, or it-1 when period == 0).
+ *     Results therefore do not depend on launch shape, grid size, or what
+ *     else runs on the GPU.
+ *   - Tabu iterations are numbered from 1.  Move (r, s) is tabu at iteration
+ *     it while tabu_until[r][s] > it; applying it at iteration it sets
+ *     tabu_until[r][s] = it + t, t = tmin + (x * (tmax - tmin + 1)) >> 32.
+ *     With aspiration on, a tabu move is admissible if cost + delta < best.
+ *   - The per-walk trajectory hash is FNV-1a/64 over the applied moves:
+ *     h = 14695981039346656037; per move h ^= (r << 16 | s); h *= 1099511628211.
+ *
+ * Arithmetic is exact integer arithmetic.  The library keeps deltas in int32
+ * when the bound B = (n^2 + 8n + 32) * max|F| * max|D| is at most
+ * 2^31 - 2, and in int64 otherwise (or when QAP_FORCE_INT64 is given).
+ *
+ * Errors: every entry point returns a qap_status; on error nothing has been
+ * written to the outputs unless stated otherwise.  A CUDA error is returned
+ * as QAP_ECUDA and the CUDA error string is kept for qap_last_error().
+ * Entry points are thread-safe for distinct contexts; one context must not
+ * be used by two host threads at once.
+ */
+#ifndef QAP_H
+#define QAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qap_ctx qap_ctx;  /* opaque: device copies of F and D */
+
+typedef enum {
+  QAP_OK = 0,
+  QAP_EINVAL = 1,        /* invalid argument (n < 2, bad permutation, ...)      */
+  QAP_EOVERFLOW = 2,     /* the bound B does not fit the int64 path (>= 2^62)   */
+  QAP_ENOMEM = 3,        /* device or host allocation failed                   */
+  QAP_ECUDA = 4,         /* a CUDA runtime call failed; see qap_last_error()   */
+  QAP_ETIMEOUT = 5,      /* a bounded wait ran out (serving loop)              */
+  QAP_EUNSUPPORTED = 6   /* instance outside the kernels' ranges: n > 181,
+                            F outside int16 or D outside int8                   */
+} qap_status;
+
+/* Tabu tenure rule: t drawn uniformly from [tmin, tmax]; a new t every
+ * `period` iterations (at it = 1, period + 1, ...), or for every applied move
+ * when period == 0 (the paper's rule, Section 4.3). */
+typedef struct {
+  int32_t tmin;
+  int32_t tmax;
+  int32_t period;
+} qap_tenure;
+
+#define QAP_FORCE_INT64 1u   /* qap_create flag: keep deltas in int64 */
+
+/* Launch forms of a search. */
+#define QAP_LAUNCH_PERSISTENT 0  /* one launch; CTAs loop over walks          */
+#define QAP_LAUNCH_PLAIN 1       /* one launch per walk (comparison form)     */
+
+typedef struct {
+  int32_t n;
+  int32_t delta_bytes;     /* 4 (int32 path) or 8 (int64 path)              */
+  int32_t sym_flow;        /* F == F^T                                      */
+  int32_t sym_dist;        /* D == D^T                                      */
+  int64_t bound;           /* B above                                       */
+} qap_ctx_info;
+
+/* Create a context for one instance.
+ *   F, D   host pointers to n*n int64 values, row-major.  Copied; the caller
+ *          may free them when the call returns.  F must fit int16 and D int8.
+ *   n      2 <= n <= 181.
+ *   flags  0 or QAP_FORCE_INT64.
+ *   out    receives the context (NULL on error).
+ * Uses the CUDA device current at the call for all later calls.
+ * Errors: QAP_EINVAL (null pointer, n < 2), QAP_EUNSUPPORTED, QAP_EOVERFLOW,
+ * QAP_ENOMEM, QAP_ECUDA. */
+qap_status qap_create(const int64_t* F, const int64_t* D, int32_t n, uint32_t flags,
+                      qap_ctx** out);
+
+/* Release a context and its device memory.  NULL is ignored. */
+void qap_destroy(qap_ctx* ctx);
+
+/* Describe a context.  Errors: QAP_EINVAL on null pointers. */
+qap_status qap_info(const qap_ctx* ctx, qap_ctx_info* out);
+
+/* Text for a status code (static storage). */
+const char* qap_strerror(qap_status s);
+
+/* Detail of the last QAP_ECUDA on this host thread (static per thread). */
+const char* qap_last_error(void);
+
+/* Eq. 1 for `count` permutations on the GPU.
+ *   p     host pointer, count x n int32, row k a permutation of 0..n-1.
+ *   cost  host pointer, count int64 outputs.
+ * Errors: QAP_EINVAL (count < 0, null pointers, a row that is not a
+ * permutation; nothing is computed), QAP_ENOMEM, QAP_ECUDA. */
+qap_status qap_cost(qap_ctx* ctx, int32_t count, const int32_t* p, int64_t* cost);
+
+/* Parameters of a search call. */
+typedef struct {
+  int32_t starts;          /* number of walks W >= 1                         */
+  uint32_t walk_base;      /* walk k uses walk id walk_base + k              */
+  int32_t descend;         /* 1: 2opt to a local minimum before tabu         */
+  int32_t max_descent;     /* cap on 2opt moves; < 0 means 2^20 (a 2opt
+                              descent ends long before on real instances) */
+  int32_t iters;           /* tabu iterations, >= 0                          */
+  qap_tenure tenure;       /* used when iters > 0: 1 <= tmin <= tmax         */
+  int32_t aspiration;      /* 0 or 1                                         */
+  uint64_t seed;           /* Philox key                                     */
+  int32_t launch;          /* QAP_LAUNCH_PERSISTENT or QAP_LAUNCH_PLAIN      */
+  int32_t threads_per_walk;/* 0 = automatic; else 128, 256, 512 or 1024      */
+} qap_search_params;
+
+/* Per-walk outputs; every pointer may be NULL except best_cost.  For
+ * qap_search they are host pointers, for qap_search_async device pointers.
+ *   best_p        W x n  best permutation of the walk
+ *   best_cost     W      its cost
+ *   final_cost    W      cost of the walk's last solution
+ *   best_iter     W      tabu iteration that reached best_cost (0 = before
+ *                        the tabu phase)
+ *   iters_done    W      tabu iterations that applied a move
+ *   status        W      0 = completed, 1 = stopped early: no admissible move
+ *   descent_moves W      moves applied by the 2opt phase
+ *   hash          W      trajectory hash of the tabu phase
+ *   descent_hash  W      trajectory hash of the 2opt phase */
+typedef struct {
+  int32_t* best_p;
+  int64_t* best_cost;
+  int64_t* final_cost;
+  int32_t* best_iter;
+  int32_t* iters_done;
+  int32_t* status;
+  int32_t* descent_moves;
+  uint64_t* hash;
+  uint64_t* descent_hash;
+} qap_walk_outputs;
+
+/* Run W independent walks of one instance; host buffers, blocking.
+ *   starts  host pointer, W x n start permutations, or NULL to draw them
+ *           (stream 0 of each walk).
+ * Host<->device copies of starts and outputs are part of the call.
+ * Errors: QAP_EINVAL (bad parameters or a start that is not a permutation;
+ * nothing is run), QAP_EUNSUPPORTED (threads_per_walk too small for n),
+ * QAP_ENOMEM, QAP_ECUDA. */
+qap_status qap_search(qap_ctx* ctx, const qap_search_params* params, const int32_t* starts,
+                      const qap_walk_outputs* out);
+
+/* Stream-ordered form of qap_search: device pointers, no synchronisation.
+ *   d_starts device pointer (W x n) or NULL.  Not validated: rows must be
+ *            permutations of 0..n-1.
+ *   out      device pointers, valid until the stream reaches the end of the
+ *            call's work.
+ *   stream   a cudaStream_t (NULL = legacy default stream).
+ * Kernel launches only; capturable into a CUDA graph once the same
+ * (n, threads_per_walk, delta width) has been run once outside capture.
+ * Errors: QAP_EINVAL, QAP_EUNSUPPORTED, QAP_ECUDA (launch errors only). */
+qap_status qap_search_async(qap_ctx* ctx, const qap_search_params* params,
+                            const int32_t* d_starts, const qap_walk_outputs* out,
+                            void* stream);
+
+/* Launch shape a search would use.  Errors: as qap_search_async. */
+typedef struct {
+  int32_t threads_per_walk;
+  int32_t pairs_per_thread;  /* register slots per thread                 */
+  int32_t smem_bytes;        /* dynamic shared memory per CTA             */
+  int32_t grid;              /* CTAs of the persistent launch             */
+  int32_t ctas_per_sm;
+  int32_t sms;
+} qap_plan_info;
+qap_status qap_plan(qap_ctx* ctx, const qap_search_params* params, qap_plan_info* out);
+
+/* Convenience forms named after the two heuristics (host buffers, blocking).
+ * qap_2opt: W walks of best-improvement 2opt to a local minimum from random
+ *   starts; iters_done receives the number of moves of each walk.
+ * qap_tabu: W walks of tabu search for `iters` iterations from random starts;
+ *   status receives 0/1 as in qap_walk_outputs.
+ * best_p (W x n) and best_cost (W) are required, the rest may be NULL. */
+qap_status qap_2opt(qap_ctx* ctx, int32_t starts, uint64_t seed, int32_t max_iters,
+                    int32_t* best_p, int64_t* best_cost, int32_t* iters_done);
+qap_status qap_tabu(qap_ctx* ctx, int32_t starts, int32_t iters, qap_tenure tenure,
+                    int32_t aspiration, uint64_t seed, int32_t* best_p, int64_t* best_cost,
+                    int32_t* best_iter, int32_t* status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QAP_H */

@@ -1,0 +1,13 @@
+"""GB300-native swap-neighbourhood QAP search (2opt and tabu search walks).
+
+The compute path is the CUDA library ``libqap.so`` (C-ABI in include/qap.h),
+bound by ``_binding``; ``instances`` holds the seeded synthetic workloads.
+Importing the package loads nothing; the library is built and loaded on the
+first call.
+"""
+from ._binding import (  # noqa: F401
+    EINVAL, ECUDA, ENOMEM, EOVERFLOW, ETIMEOUT, EUNSUPPORTED, FORCE_INT64, LAUNCH_PERSISTENT,
+    LAUNCH_PLAIN, OK, Instance, QapError, SearchParams, Tenure, WalkOutputs, lib, make_params,
+    qap_2opt, qap_cost, qap_create, qap_destroy, qap_info, qap_plan, qap_search,
+    qap_search_async, qap_tabu, strerror, last_error,
+)

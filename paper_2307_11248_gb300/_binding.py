@@ -1,0 +1,277 @@
+"""Thin ctypes binding of ``libqap.so`` (include/qap.h).
+
+Argument marshalling only: every step of the search runs in the CUDA
+library.  Function names follow the C-ABI.  There is no fallback: if the
+library cannot be built or loaded, or no CUDA device is usable, the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, EOVERFLOW, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(7)
+FORCE_INT64 = 1
+LAUNCH_PERSISTENT, LAUNCH_PLAIN = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class QapError(RuntimeError):
+    def __init__(self, status, where):
+        msg = f"{where}: {strerror(status)}"
+        if status == ECUDA:
+            msg += f" ({last_error()})"
+        super().__init__(msg)
+        self.status = status
+
+
+class Tenure(ctypes.Structure):
+    _fields_ = [("tmin", ctypes.c_int32), ("tmax", ctypes.c_int32), ("period", ctypes.c_int32)]
+
+
+class CtxInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("delta_bytes", ctypes.c_int32),
+                ("sym_flow", ctypes.c_int32), ("sym_dist", ctypes.c_int32),
+                ("bound", ctypes.c_int64)]
+
+
+class SearchParams(ctypes.Structure):
+    _fields_ = [("starts", ctypes.c_int32), ("walk_base", ctypes.c_uint32),
+                ("descend", ctypes.c_int32), ("max_descent", ctypes.c_int32),
+                ("iters", ctypes.c_int32), ("tenure", Tenure), ("aspiration", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("launch", ctypes.c_int32),
+                ("threads_per_walk", ctypes.c_int32)]
+
+
+class WalkOutputs(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in
+                ("best_p", "best_cost", "final_cost", "best_iter", "iters_done", "status",
+                 "descent_moves", "hash", "descent_hash")]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int32) for name in
+                ("threads_per_walk", "pairs_per_thread", "smem_bytes", "grid", "ctas_per_sm",
+                 "sms")]
+
+
+OUTPUT_FIELDS = {  # name -> (dtype, per-walk shape multiplier uses n)
+    "best_p": (np.int32, True), "best_cost": (np.int64, False), "final_cost": (np.int64, False),
+    "best_iter": (np.int32, False), "iters_done": (np.int32, False), "status": (np.int32, False),
+    "descent_moves": (np.int32, False), "hash": (np.uint64, False),
+    "descent_hash": (np.uint64, False),
+}
+
+
+def lib():
+    """Build (if stale) and load the CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            vp, i32, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64
+            st = ctypes.c_int
+            L.qap_create.argtypes = [vp, vp, i32, u32, ctypes.POINTER(vp)]
+            L.qap_create.restype = st
+            L.qap_destroy.argtypes = [vp]
+            L.qap_destroy.restype = None
+            L.qap_info.argtypes = [vp, ctypes.POINTER(CtxInfo)]
+            L.qap_info.restype = st
+            L.qap_strerror.argtypes = [st]
+            L.qap_strerror.restype = ctypes.c_char_p
+            L.qap_last_error.argtypes = []
+            L.qap_last_error.restype = ctypes.c_char_p
+            L.qap_cost.argtypes = [vp, i32, vp, vp]
+            L.qap_cost.restype = st
+            L.qap_search.argtypes = [vp, ctypes.POINTER(SearchParams), vp,
+                                     ctypes.POINTER(WalkOutputs)]
+            L.qap_search.restype = st
+            L.qap_search_async.argtypes = [vp, ctypes.POINTER(SearchParams), vp,
+                                           ctypes.POINTER(WalkOutputs), vp]
+            L.qap_search_async.restype = st
+            L.qap_plan.argtypes = [vp, ctypes.POINTER(SearchParams), ctypes.POINTER(PlanInfo)]
+            L.qap_plan.restype = st
+            L.qap_2opt.argtypes = [vp, i32, u64, i32, vp, vp, vp]
+            L.qap_2opt.restype = st
+            L.qap_tabu.argtypes = [vp, i32, i32, Tenure, i32, u64, vp, vp, vp, vp]
+            L.qap_tabu.restype = st
+            _lib = L
+    return _lib
+
+
+def strerror(status):
+    return lib().qap_strerror(status).decode()
+
+
+def last_error():
+    return lib().qap_last_error().decode()
+
+
+def _check(status, where):
+    if status != OK:
+        raise QapError(status, where)
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
+
+
+def make_params(starts, *, seed=0, iters=0, tenure=(1, 1, 0), aspiration=True, descend=False,
+                max_descent=-1, walk_base=0, launch=LAUNCH_PERSISTENT, threads_per_walk=0):
+    return SearchParams(int(starts), int(walk_base), int(bool(descend)), int(max_descent),
+                        int(iters), Tenure(*[int(t) for t in tenure]), int(bool(aspiration)),
+                        int(seed) & (2**64 - 1), int(launch), int(threads_per_walk))
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C-ABI)
+# ---------------------------------------------------------------------------
+
+def qap_create(F, D, flags=0):
+    F = np.ascontiguousarray(F, dtype=np.int64)
+    D = np.ascontiguousarray(D, dtype=np.int64)
+    n = F.shape[0]
+    if F.shape != (n, n) or D.shape != (n, n):
+        raise ValueError("F and D must be n x n")
+    h = ctypes.c_void_p()
+    _check(lib().qap_create(_ptr(F), _ptr(D), n, flags, ctypes.byref(h)), "qap_create")
+    return h
+
+
+def qap_destroy(h):
+    lib().qap_destroy(h)
+
+
+def qap_info(h):
+    info = CtxInfo()
+    _check(lib().qap_info(h, ctypes.byref(info)), "qap_info")
+    return {k: getattr(info, k) for k, _ in CtxInfo._fields_}
+
+
+def qap_cost(h, perms):
+    P = np.ascontiguousarray(perms, dtype=np.int32)
+    if P.ndim == 1:
+        P = P[None, :]
+    out = np.zeros(P.shape[0], dtype=np.int64)
+    _check(lib().qap_cost(h, P.shape[0], _ptr(P), _ptr(out)), "qap_cost")
+    return out
+
+
+def qap_plan(h, params):
+    info = PlanInfo()
+    _check(lib().qap_plan(h, ctypes.byref(params), ctypes.byref(info)), "qap_plan")
+    return {k: getattr(info, k) for k, _ in PlanInfo._fields_}
+
+
+def qap_search(h, params, starts=None, n=None):
+    """Blocking search with host buffers; returns a dict of numpy arrays."""
+    if n is None:
+        n = qap_info(h)["n"]
+    W = params.starts
+    st = None
+    if starts is not None:
+        st = np.ascontiguousarray(starts, dtype=np.int32)
+        if st.shape != (W, n):
+            raise ValueError("starts must be W x n")
+    out = {k: np.zeros((W, n) if per_n else W, dtype=dt)
+           for k, (dt, per_n) in OUTPUT_FIELDS.items()}
+    o = WalkOutputs(**{k: out[k].ctypes.data for k in OUTPUT_FIELDS})
+    _check(lib().qap_search(h, ctypes.byref(params), _ptr(st), ctypes.byref(o)), "qap_search")
+    return out
+
+
+def qap_search_async(h, params, d_starts, d_out, stream):
+    """Stream-ordered search on device pointers.
+
+    d_starts: device pointer (int) or 0; d_out: dict name -> device pointer
+    (int; missing names are NULL); stream: cudaStream_t as an int."""
+    o = WalkOutputs(**{k: int(d_out.get(k, 0) or 0) for k in OUTPUT_FIELDS})
+    _check(lib().qap_search_async(h, ctypes.byref(params), ctypes.c_void_p(int(d_starts or 0)),
+                                  ctypes.byref(o), ctypes.c_void_p(int(stream or 0))),
+           "qap_search_async")
+
+
+def qap_2opt(h, starts, seed, max_iters=-1, n=None):
+    if n is None:
+        n = qap_info(h)["n"]
+    best_p = np.zeros((starts, n), dtype=np.int32)
+    best_cost = np.zeros(starts, dtype=np.int64)
+    moves = np.zeros(starts, dtype=np.int32)
+    _check(lib().qap_2opt(h, starts, int(seed), max_iters, _ptr(best_p), _ptr(best_cost),
+                          _ptr(moves)), "qap_2opt")
+    return best_p, best_cost, moves
+
+
+def qap_tabu(h, starts, iters, tenure, aspiration, seed, n=None):
+    if n is None:
+        n = qap_info(h)["n"]
+    best_p = np.zeros((starts, n), dtype=np.int32)
+    best_cost = np.zeros(starts, dtype=np.int64)
+    best_iter = np.zeros(starts, dtype=np.int32)
+    status = np.zeros(starts, dtype=np.int32)
+    _check(lib().qap_tabu(h, starts, iters, Tenure(*tenure), int(bool(aspiration)), int(seed),
+                          _ptr(best_p), _ptr(best_cost), _ptr(best_iter), _ptr(status)),
+           "qap_tabu")
+    return best_p, best_cost, best_iter, status
+
+
+# ---------------------------------------------------------------------------
+# convenience: an instance handle and torch device buffers
+# ---------------------------------------------------------------------------
+
+class Instance:
+    """Owns one qap_ctx; use as a context manager or call close()."""
+
+    def __init__(self, F, D, force_int64=False):
+        self.n = int(np.asarray(F).shape[0])
+        self.h = qap_create(F, D, FORCE_INT64 if force_int64 else 0)
+        self.info = qap_info(self.h)
+
+    def close(self):
+        if self.h is not None:
+            qap_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cost(self, perms):
+        return qap_cost(self.h, perms)
+
+    def plan(self, params):
+        return qap_plan(self.h, params)
+
+    def search(self, params, starts=None):
+        return qap_search(self.h, params, starts, n=self.n)
+
+    def device_outputs(self, walks, device="cuda"):
+        """torch tensors for every output of a search of `walks` walks."""
+        import torch
+        tdt = {np.int32: torch.int32, np.int64: torch.int64, np.uint64: torch.int64}
+        return {k: torch.zeros((walks, self.n) if per_n else walks, dtype=tdt[dt], device=device)
+                for k, (dt, per_n) in OUTPUT_FIELDS.items()}
+
+    def search_async(self, params, outs, starts=None, stream=None):
+        """Stream-ordered search into torch tensors from device_outputs()."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        d_out = {k: v.data_ptr() for k, v in outs.items()}
+        qap_search_async(self.h, params, starts.data_ptr() if starts is not None else 0, d_out,
+                         stream.cuda_stream)

@@ -1,0 +1,56 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/qap.h (no GPU needed: nothing is called)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            with open(os.path.join(ROOT, "include", fn)) as f:
+                text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+            names.update(re.findall(r"\b(qap_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for required in ["qap_create", "qap_destroy", "qap_cost", "qap_2opt", "qap_tabu",
+                     "qap_search", "qap_search_async", "qap_strerror"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2307_11248_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_without_gpu():
+    import paper_2307_11248_gb300 as q
+    assert q.strerror(q.EINVAL) == "invalid argument"
+    assert q.strerror(q.EUNSUPPORTED).startswith("instance outside")
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu():
+    import numpy as np
+    import paper_2307_11248_gb300 as q
+    with pytest.raises(q.QapError) as e:
+        q.qap_create(np.zeros((1, 1)), np.zeros((1, 1)))
+    assert e.value.status == q.EINVAL
+    big = np.zeros((4, 4), dtype=np.int64)
+    big[0, 1] = 300  # D outside int8
+    with pytest.raises(q.QapError) as e:
+        q.qap_create(np.zeros((4, 4)), big)
+    assert e.value.status == q.EUNSUPPORTED
+    with pytest.raises(q.QapError) as e:
+        q.qap_create(np.zeros((200, 200)), np.zeros((200, 200)))
+    assert e.value.status == q.EUNSUPPORTED
