@@ -209,6 +209,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-walk-per-launch form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--threads-per-walk", type=int, default=0)
+    ap.add_argument("--iters", type=int, default=0,
+                    help="override the iteration count (smaller cases for profiling)")
+    ap.add_argument("--walks", type=int, default=0, help="override the walk count")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -222,6 +225,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = workload()
+    if args.iters:
+        w["iters"] = args.iters
+    if args.walks:
+        w["walks"] = args.walks
     n, T, W, iters = w["n"], w["pairs"], w["walks"], w["iters"]
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -324,7 +331,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32" if dbytes == 4 else "int64",
         "data": "synthetic",
-        "config": {"workload": "tabu n=50 asym uniform[0,99], 256 walks x 5000 iters",
+        "config": {"workload": f"tabu n=50 asym uniform[0,99], {W} walks x {iters} iters",
                    "n": n, "walks_per_gpu": W, "iters": iters, "tenure": list(w["tenure"]),
                    "aspiration": True, "launch": "persistent, one launch per step",
                    "threads_per_walk": plan["threads_per_walk"], "grid": plan["grid"],

@@ -16,8 +16,9 @@
 #include "qap_kernels.cuh"
 
 namespace qapk {
-WalkKernelFn walk_kernel_i32(int nt, int maxpt);
-WalkKernelFn walk_kernel_i64(int nt, int maxpt);
+WalkKernelFn walk_kernel_i32_f8(int nt, int maxpt);
+WalkKernelFn walk_kernel_i32_f16(int nt, int maxpt);
+WalkKernelFn walk_kernel_i64_f16(int nt, int maxpt);
 }  // namespace qapk
 
 namespace {
@@ -52,12 +53,13 @@ struct qap_ctx {
   int device = 0;
   int n = 0, ldF = 0, ldP = 0;
   int symF = 0, symD = 0;
-  int dbytes = 4;
+  int dbytes = 4;  // delta width
+  int fbytes = 2;  // flow element width in device memory (1: int8, 2: int16)
   int64_t bound = 0;
   int sms = 0;
   int smem_optin = 0;
-  int16_t* dF = nullptr;
-  int16_t* dFt = nullptr;
+  void* dF = nullptr;
+  void* dFt = nullptr;
   int8_t* dD = nullptr;
   cudaStream_t stream = nullptr;
   // growable device buffers for the blocking entry points
@@ -72,8 +74,8 @@ using KernelFn = qapk::WalkKernelFn;
 // Register plans (threads per walk, pair slots per thread) compiled into the
 // library.  The automatic choice takes the fewest threads that keep at most
 // six pairs per thread, then the fewest slots that hold them all.
-const Plan kPlans[] = {{128, 4},  {128, 8},   {256, 4},   {256, 8},  {512, 4},
-                       {512, 8},  {1024, 8},  {1024, 12}, {1024, 16}};
+const Plan kPlans[] = {{128, 4},  {128, 12}, {256, 6},  {256, 8},   {512, 4},
+                       {512, 8},  {512, 12}, {1024, 8}, {1024, 12}, {1024, 16}};
 
 bool choose_plan(int n, int threads, Plan* out) {
   const int T = n * (n - 1) / 2;
@@ -94,6 +96,12 @@ bool choose_plan(int n, int threads, Plan* out) {
   return false;
 }
 
+KernelFn pick_kernel(const qap_ctx* ctx, const Plan& p) {
+  if (ctx->dbytes == 8) return qapk::walk_kernel_i64_f16(p.nt, p.maxpt);
+  if (ctx->fbytes == 1) return qapk::walk_kernel_i32_f8(p.nt, p.maxpt);
+  return qapk::walk_kernel_i32_f16(p.nt, p.maxpt);
+}
+
 std::mutex g_attr_mu;
 
 qap_status prepare_kernel(KernelFn fn, int smem) {
@@ -107,6 +115,7 @@ qap_status prepare_kernel(KernelFn fn, int smem) {
 struct Launch {
   KernelFn fn;
   Plan plan;
+  int group;  // lanes per recompute task
   int smem;
   int ctas_per_sm;
   int grid;
@@ -131,11 +140,11 @@ qap_status validate_params(const qap_ctx* ctx, const qap_search_params* p) {
 
 qap_status plan_launch(qap_ctx* ctx, const qap_search_params* p, Launch* L) {
   if (!choose_plan(ctx->n, p->threads_per_walk, &L->plan)) return QAP_EUNSUPPORTED;
-  L->fn = ctx->dbytes == 4 ? qapk::walk_kernel_i32(L->plan.nt, L->plan.maxpt)
-                           : qapk::walk_kernel_i64(L->plan.nt, L->plan.maxpt);
+  L->fn = pick_kernel(ctx, L->plan);
   if (!L->fn) return QAP_EUNSUPPORTED;
   const qapk::SmemLayout S =
-      qapk::smem_layout(ctx->n, ctx->ldF, ctx->ldP, ctx->symF, ctx->symD, ctx->dbytes);
+      qapk::smem_layout(ctx->n, ctx->ldF, ctx->fbytes, ctx->ldP, ctx->symF, ctx->symD,
+                        ctx->dbytes);
   L->smem = S.bytes;
   if (L->smem > ctx->smem_optin) return QAP_EUNSUPPORTED;
   qap_status st = prepare_kernel(L->fn, L->smem);
@@ -146,6 +155,11 @@ qap_status plan_launch(qap_ctx* ctx, const qap_search_params* p, Launch* L) {
   if (occ < 1) return QAP_EUNSUPPORTED;
   L->ctas_per_sm = occ;
   L->grid = std::min(p->starts, occ * ctx->sms);
+  // widest power-of-two group (<= 8 lanes, <= the row chunks) that still
+  // gives every (row, index) task of phase X its own group
+  const int nc = (ctx->n + 16 / ctx->fbytes - 1) / (16 / ctx->fbytes);
+  L->group = 8;
+  while (L->group > 1 && (L->plan.nt / L->group < 2 * ctx->n || L->group > nc)) L->group >>= 1;
   return QAP_OK;
 }
 
@@ -249,12 +263,16 @@ qap_status qap_create(const int64_t* F, const int64_t* D, int32_t n, uint32_t fl
   qap_ctx* c = new (std::nothrow) qap_ctx();
   if (!c) return QAP_ENOMEM;
   c->n = n;
-  c->ldF = round_up(n, 8);
-  c->ldP = round_up(n, 16);
   c->symF = symF;
   c->symD = symD;
   c->bound = bound;
   c->dbytes = ((flags & QAP_FORCE_INT64) || bound > (int64_t)INT_MAX - 1) ? 8 : 4;
+  // int8 flows (dp4a rows) when they fit and deltas are int32; else int16
+  c->fbytes = (mF <= 127 && c->dbytes == 4) ? 1 : 2;
+  c->ldF = round_up(n, 16 / c->fbytes);
+  // P rows: an odd number of 16-byte chunks, so the column exchanges of a
+  // move hit 8 different banks per 32 rows instead of 2
+  c->ldP = 16 * (((n + 15) / 16) | 1);
   auto fail = [&](qap_status s) {
     qap_destroy(c);
     return s;
@@ -265,20 +283,37 @@ qap_status qap_create(const int64_t* F, const int64_t* D, int32_t n, uint32_t fl
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
   e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
-  std::vector<int16_t> hF((size_t)n * c->ldF, 0), hFt((size_t)n * c->ldF, 0);
+  const size_t fcount = (size_t)n * c->ldF;
+  std::vector<int16_t> hF16, hFt16;
+  std::vector<int8_t> hF8, hFt8;
+  if (c->fbytes == 1) {
+    hF8.assign(fcount, 0);
+    hFt8.assign(fcount, 0);
+  } else {
+    hF16.assign(fcount, 0);
+    hFt16.assign(fcount, 0);
+  }
   std::vector<int8_t> hD((size_t)n * n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
-      hF[(size_t)i * c->ldF + j] = (int16_t)F[(size_t)i * n + j];
-      hFt[(size_t)j * c->ldF + i] = (int16_t)F[(size_t)i * n + j];
+      const int64_t f = F[(size_t)i * n + j];
+      if (c->fbytes == 1) {
+        hF8[(size_t)i * c->ldF + j] = (int8_t)f;
+        hFt8[(size_t)j * c->ldF + i] = (int8_t)f;
+      } else {
+        hF16[(size_t)i * c->ldF + j] = (int16_t)f;
+        hFt16[(size_t)j * c->ldF + i] = (int16_t)f;
+      }
       hD[(size_t)i * n + j] = (int8_t)D[(size_t)i * n + j];
     }
-  const size_t fbytes = hF.size() * sizeof(int16_t);
+  const void* srcF = c->fbytes == 1 ? (const void*)hF8.data() : (const void*)hF16.data();
+  const void* srcFt = c->fbytes == 1 ? (const void*)hFt8.data() : (const void*)hFt16.data();
+  const size_t fbytes = fcount * c->fbytes;
   if (cudaMalloc(&c->dF, fbytes) != cudaSuccess) return fail(QAP_ENOMEM);
   if (!symF && cudaMalloc(&c->dFt, fbytes) != cudaSuccess) return fail(QAP_ENOMEM);
   if (cudaMalloc(&c->dD, hD.size()) != cudaSuccess) return fail(QAP_ENOMEM);
-  e = cudaMemcpy(c->dF, hF.data(), fbytes, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !symF) e = cudaMemcpy(c->dFt, hFt.data(), fbytes, cudaMemcpyHostToDevice);
+  e = cudaMemcpy(c->dF, srcF, fbytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !symF) e = cudaMemcpy(c->dFt, srcFt, fbytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->dD, hD.data(), hD.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
   e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
@@ -337,6 +372,7 @@ qap_status qap_search_async(qap_ctx* ctx, const qap_search_params* params,
   if (st != QAP_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   qapk::WalkArgs a = make_args(ctx, params, d_starts, out);
+  a.group = L.group;
   if (params->launch == QAP_LAUNCH_PLAIN) {
     a.walks = 1;
     for (int w = 0; w < params->starts; ++w) {
@@ -424,7 +460,12 @@ qap_status qap_cost(qap_ctx* ctx, int32_t count, const int32_t* p, int64_t* cost
   cudaStream_t s = ctx->stream;
   QAP_CUDA(cudaMemcpyAsync(dp, p, pbytes, cudaMemcpyHostToDevice, s));
   const int grid = std::min(count, ctx->sms * 8);
-  qapk::cost_kernel<256><<<grid, 256, 0, s>>>(ctx->dF, ctx->ldF, ctx->dD, n, dp, count, dc);
+  if (ctx->fbytes == 1)
+    qapk::cost_kernel<int8_t, 256><<<grid, 256, 0, s>>>(static_cast<const int8_t*>(ctx->dF),
+                                                        ctx->ldF, ctx->dD, n, dp, count, dc);
+  else
+    qapk::cost_kernel<int16_t, 256><<<grid, 256, 0, s>>>(static_cast<const int16_t*>(ctx->dF),
+                                                         ctx->ldF, ctx->dD, n, dp, count, dc);
   QAP_CUDA(cudaGetLastError());
   QAP_CUDA(cudaMemcpyAsync(cost, dc, (size_t)count * 8, cudaMemcpyDeviceToHost, s));
   QAP_CUDA(cudaStreamSynchronize(s));

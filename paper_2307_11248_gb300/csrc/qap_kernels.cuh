@@ -2,30 +2,44 @@
 //
 // One CTA runs one search walk at a time and loops over walks (persistent
 // form).  Per walk everything lives on chip:
-//   shared memory   F (int16) and, for an asymmetric flow, its transpose;
-//                   P = D[p][p] (int8) and, for asymmetric distances, its
-//                   transpose; the tabu table (int32 per pair); the four
-//                   O(1)-update vectors; the two recomputed delta rows;
-//                   p and the best permutation.
+//   shared memory   F (int8 when every |F| <= 127, else int16) and, for an
+//                   asymmetric flow, F^T; P = D[p][p] (int8) and, for
+//                   asymmetric distances, P^T; the tabu table (int32 per
+//                   pair); the O(1)-update vectors; two recomputed delta
+//                   rows; g[k] = sum_j F[k][j]P[k][j] + F[j][k]P[j][k]
+//                   (double-buffered); p and the best permutation.
 //   registers       the delta of every pair the thread owns (thread t owns
-//                   pairs t, t + NT, t + 2 NT, ... of the lexicographic
-//                   pair order) and the packed (r << 8 | s) key of each.
+//                   pairs t, t + NT, t + 2 NT, ... of the lexicographic pair
+//                   order) and the packed (r << 8 | s) key of each.
 //
-// One iteration (Sections 4.1, 4.3):
-//   scan    each thread filters its pairs (tabu / aspiration) and keeps the
-//           lowest (delta, key); warp REDUX min, then one CTA-wide round
-//           through shared memory gives every thread the chosen move;
-//   apply   swap p[r], p[s]; swap rows and columns r, s of P (and P^T);
-//           cost += delta; tabu stamp by the owner of (r, s);
-//   update  pairs disjoint from {r, s}: O(1) update from the vectors
-//             a_x = F[r][x]-F[s][x], b_x = P'[s][x]-P'[r][x],
-//             c_x = F[x][r]-F[x][s], e_x = P'[x][s]-P'[x][r]
-//           (delta += (a_u-a_v)(b_u-b_v) + (c_u-c_v)(e_u-e_v));
-//           pairs touching r or s: Eq. 2 recomputed by 8-lane groups;
-//           pair (r, s): negated.
+// One tabu iteration, move (r, s) already chosen, has two barriers:
+//   phase X  (reads the pre-move P, called Q below)  one task per index k:
+//            k outside {r, s}: the Eq. 2 deltas of pairs {r, k} and {s, k}
+//            after the move, by dp4a (int8 F) or dp2a (int16 F) dot
+//            products of F / F^T rows with Q / Q^T rows plus O(1)
+//            corrections; the update vectors of k; g'[k] = g[k] - a_k b_k
+//            - c_k e_k.
+//            k in {r, s}: g'[k] by dot products.
+//   -- barrier --
+//   phase Y  owners update their deltas: pairs disjoint from {r, s} by
+//            delta += (a_u-a_v)(b_u-b_v) + (c_u-c_v)(e_u-e_v) with
+//              a_x = F[r][x]-F[s][x], b_x = P'[s][x]-P'[r][x],
+//              c_x = F[x][r]-F[x][s], e_x = P'[x][s]-P'[x][r];
+//            pairs touching r or s from the recomputed rows; pair (r, s)
+//            negated; in the same pass each updated delta enters the scan of
+//            the next iteration (tabu / aspiration filter, lowest
+//            (delta, r, s)).  Rows and columns r, s of P (and P^T) are then
+//            exchanged and p[r], p[s] swapped.
+//   -- barrier --  (inside the CTA arg-min: warp REDUX, then one round
+//                   through shared memory)
+// Dot products over all j count the j = x and j = k terms; removing them and
+// adding the two fixed terms of Eq. 2 leaves one product,
+//   (F[x][x]-F[x][k]-F[k][x]+F[k][k]) (P'[x][x]-P'[x][k]-P'[k][x]+P'[k][k]).
+// The dot with a post-move row is the dot with the pre-move row plus a
+// correction for the two exchanged columns.
 #pragma once
-#include <cstdint>
 #include <climits>
+#include <cstdint>
 
 #include "qap_philox.cuh"
 
@@ -33,15 +47,15 @@ namespace qapk {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kNoMove = 0xffffffffu;
-constexpr uint32_t kNoPair = 0xffffu;  // packed-key slot without a pair
-constexpr int kGroup = 8;  // lanes per recomputed pair
-constexpr int kDescentCap = 1 << 20;  // 2opt moves when no cap is given
+constexpr uint32_t kNoPair = 0xffffu;     // packed-key slot without a pair
+constexpr int kDescentCap = 1 << 20;      // 2opt moves when no cap is given
 
 struct WalkArgs {
-  int n, ldF, ldP;
+  int n, ldF, ldP;    // ldF: elements per F row; ldP: bytes per P row
   int symF, symD;
-  const int16_t* F;   // n x ldF, row-major, padded
-  const int16_t* Ft;  // transpose of F (== F when symF)
+  int group;          // lanes per phase-X task (1, 2, 4 or 8)
+  const void* F;      // n x ldF (int8 or int16), row-major, zero padded
+  const void* Ft;     // transpose of F (== F when symF)
   const int8_t* D;    // n x n, row-major
   int walks;          // walks processed by this launch
   int walk_offset;    // index of this launch's first walk in the outputs
@@ -65,24 +79,27 @@ struct WalkArgs {
 // shared-memory layout (host and device agree through this function)
 // ---------------------------------------------------------------------------
 struct SmemLayout {
-  int offF, offFt, offP, offPt, offTabu, offVec, offR, offPerm, offBest, offRedD, offRedK, offSum;
+  int offF, offFt, offP, offPt, offTabu, offVec, offR, offG0, offG1, offPerm, offBest, offRedD,
+      offRedK, offSum;
   int bytes;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline SmemLayout smem_layout(int n, int ldF, int ldP, int symF, int symD,
-                                                  int dbytes) {
+__host__ __device__ inline SmemLayout smem_layout(int n, int ldF, int fbytes, int ldP, int symF,
+                                                  int symD, int dbytes) {
   SmemLayout L;
   const int T = n * (n - 1) / 2;
   int o = 0;
-  L.offF = o;    o = align16(o + n * ldF * 2);
-  L.offFt = o;   o = symF ? o : align16(o + n * ldF * 2);
+  L.offF = o;    o = align16(o + n * ldF * fbytes);
+  L.offFt = o;   o = symF ? o : align16(o + n * ldF * fbytes);
   L.offP = o;    o = align16(o + n * ldP);
   L.offPt = o;   o = symD ? o : align16(o + n * ldP);
   L.offTabu = o; o = align16(o + T * 4);
   L.offVec = o;  o = align16(o + n * 16);
   L.offR = o;    o = align16(o + 2 * n * dbytes);
+  L.offG0 = o;   o = align16(o + n * dbytes);
+  L.offG1 = o;   o = align16(o + n * dbytes);
   L.offPerm = o; o = align16(o + n * 4);
   L.offBest = o; o = align16(o + n * 4);
   L.offRedD = o; o = align16(o + 32 * 8);
@@ -95,6 +112,35 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int ldF, int ldP, int s
 template <typename DT> struct DeltaMax;
 template <> struct DeltaMax<int32_t> { static constexpr int32_t v = INT_MAX; };
 template <> struct DeltaMax<int64_t> { static constexpr int64_t v = LLONG_MAX; };
+
+// ---------------------------------------------------------------------------
+// row chunks: F rows as int8 (16 per chunk, dp4a) or int16 (8, dp2a)
+// ---------------------------------------------------------------------------
+template <typename FE> struct Chunk;
+
+template <> struct Chunk<int8_t> {
+  static constexpr int W = 16;
+  using FV = int4;
+  using QV = int4;
+  __device__ __forceinline__ static int dot(const FV f, const QV q, int acc) {
+    acc = __dp4a(f.x, q.x, acc);
+    acc = __dp4a(f.y, q.y, acc);
+    acc = __dp4a(f.z, q.z, acc);
+    return __dp4a(f.w, q.w, acc);
+  }
+};
+
+template <> struct Chunk<int16_t> {
+  static constexpr int W = 8;
+  using FV = int4;
+  using QV = int2;
+  __device__ __forceinline__ static int dot(const FV f, const QV q, int acc) {
+    acc = __dp2a_lo(f.x, q.x, acc);
+    acc = __dp2a_hi(f.y, q.x, acc);
+    acc = __dp2a_lo(f.z, q.y, acc);
+    return __dp2a_hi(f.w, q.y, acc);
+  }
+};
 
 // ---------------------------------------------------------------------------
 // arg-min of (delta, key) across a warp, then across the CTA
@@ -148,18 +194,24 @@ __device__ __forceinline__ uint64_t fnv_step(uint64_t h, uint32_t r, uint32_t s)
   return (h ^ (uint64_t)((r << 16) | s)) * 1099511628211ull;
 }
 
+__device__ __forceinline__ unsigned group_mask(int G) {
+  return (G == 32 ? kFull : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
+}
+
 // ---------------------------------------------------------------------------
 // per-walk state views
 // ---------------------------------------------------------------------------
-template <typename DT>
+template <typename DT, typename FE>
 struct WalkSmem {
-  int16_t* F;
-  int16_t* Ft;
+  FE* F;
+  FE* Ft;
   int8_t* P;
   int8_t* Pt;
   int32_t* tabu;
   int4* vec;
   DT* R;
+  DT* g0;
+  DT* g1;
   int32_t* perm;
   int32_t* best;
   DT* redD;
@@ -167,17 +219,18 @@ struct WalkSmem {
   int64_t* sum;
 };
 
-// Eq. 2 (with the diagonal term) for the pair {x, k}, by one thread.  The
-// column terms of Eq. 2 read the transposed copies so every access is a row.
-template <typename DT>
-__device__ __forceinline__ DT delta_serial(const WalkSmem<DT>& S, int n, int ldF, int ldP,
-                                           int sym, int x, int k) {
-  const int16_t* Fx = S.F + x * ldF;
-  const int16_t* Fk = S.F + k * ldF;
+// Eq. 2 (with the diagonal term) for the pair {x, k}, by one thread, from the
+// current P.  The column terms read the transposed copies so every access is
+// along a row.  Used for the initial deltas of a walk.
+template <typename DT, typename FE>
+__device__ __forceinline__ DT delta_serial(const WalkSmem<DT, FE>& S, int n, int ldF, int ldP,
+                                           bool sym, int x, int k) {
+  const FE* Fx = S.F + x * ldF;
+  const FE* Fk = S.F + k * ldF;
   const int8_t* Px = S.P + x * ldP;
   const int8_t* Pk = S.P + k * ldP;
-  const int16_t* Ftx = S.Ft + x * ldF;
-  const int16_t* Ftk = S.Ft + k * ldF;
+  const FE* Ftx = S.Ft + x * ldF;
+  const FE* Ftk = S.Ft + k * ldF;
   const int8_t* Ptx = S.Pt + x * ldP;
   const int8_t* Ptk = S.Pt + k * ldP;
   DT acc = 0;
@@ -196,128 +249,166 @@ __device__ __forceinline__ DT delta_serial(const WalkSmem<DT>& S, int n, int ldF
   return acc + (DT)fixed + (DT)diag;
 }
 
-// Apply move (r, s) to p and P (and P^T), then build the update vectors and
-// the two recomputed delta rows.  Ends after a CTA barrier with S.vec and
-// S.R valid for the owners' update.  `copy_best` also copies p' into best.
-template <typename DT, int NT>
-__device__ __forceinline__ void apply_move(const WalkSmem<DT>& S, int n, int ldF, int ldP,
-                                           int symF, int symD, int r, int s, bool copy_best) {
-  const int tid = threadIdx.x;
-  const bool sym = symF && symD;
-  if (tid == 0) {
-    const int32_t t = S.perm[r];
-    S.perm[r] = S.perm[s];
-    S.perm[s] = t;
+// g[k] for every k from the current P (one task per k, lanes over chunks).
+template <typename DT, typename FE, int NT>
+__device__ __forceinline__ void compute_g(const WalkSmem<DT, FE>& S, DT* g, int n, int ldF,
+                                          int ldP, bool sym, int G) {
+  using C = Chunk<FE>;
+  const int lg = threadIdx.x & (G - 1);
+  const int grp = threadIdx.x / G;
+  const int NG = NT / G;
+  const int nc = (n + C::W - 1) / C::W;
+  const unsigned gmask = group_mask(G);
+  for (int k = grp; k < n; k += NG) {
+    const auto* Fk = reinterpret_cast<const typename C::FV*>(S.F + k * ldF);
+    const auto* Pk = reinterpret_cast<const typename C::QV*>(S.P + k * ldP);
+    const auto* Ftk = reinterpret_cast<const typename C::FV*>(S.Ft + k * ldF);
+    const auto* Ptk = reinterpret_cast<const typename C::QV*>(S.Pt + k * ldP);
+    int acc = 0;
+    for (int c = lg; c < nc; c += G) {
+      acc = C::dot(Fk[c], Pk[c], acc);
+      if (!sym) acc = C::dot(Ftk[c], Ptk[c], acc);
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o);
+    if (lg == 0) g[k] = sym ? (DT)2 * (DT)acc : (DT)acc;
   }
-  // P' = P with rows r, s and columns r, s exchanged.
+}
+
+// Phase X of move (r, s): see the file header.  One task per (row xi, index
+// k), xi = 0 for the pairs {r, k} and 1 for {s, k}; G lanes per task split the
+// row chunks.  The task k = x of row xi computes g'[x] instead, the task
+// k = xb (the other index of the move) has nothing to do.  Reads Q = P before
+// the move and gc = g of the pre-move state; writes vec, R (rows {r,k} and
+// {s,k} without their -g'[x] term) and gn = g after the move.
+template <typename DT, typename FE, int NT>
+__device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc, DT* gn, int n,
+                                        int ldF, int ldP, bool sym, int G, int r, int s) {
+  using C = Chunk<FE>;
+  using FV = typename C::FV;
+  using QV = typename C::QV;
+  const int lg = threadIdx.x & (G - 1);
+  const int grp = threadIdx.x / G;
+  const int NG = NT / G;
+  const int nc = (n + C::W - 1) / C::W;
+  const unsigned gmask = group_mask(G);
+  const FE* F = S.F;
+  const int8_t* Q = S.P;
+  const FE* Ft = S.Ft;
+  const int8_t* Qt = S.Pt;
+  for (int t = grp; t < 2 * n; t += NG) {
+    const int xi = t & 1, k = t >> 1;
+    const int x = xi ? s : r, xb = xi ? r : s;
+    if (k == xb) continue;  // uniform per group
+    const bool gtask = (k == x);
+    // k-task: A = F[x].Q[k] + F^T[x].Q^T[k], B = F[k].Q[xb] + F^T[k].Q^T[xb]
+    // g-task: the row paired with x is xb, so A = F[x].Q[xb] + F^T[x].Q^T[xb]
+    const int kr = gtask ? xb : k;
+    const FV* Fx = reinterpret_cast<const FV*>(F + x * ldF);
+    const FV* Ftx = reinterpret_cast<const FV*>(Ft + x * ldF);
+    const FV* Fk = reinterpret_cast<const FV*>(F + kr * ldF);
+    const FV* Ftk = reinterpret_cast<const FV*>(Ft + kr * ldF);
+    const QV* Qk = reinterpret_cast<const QV*>(Q + kr * ldP);
+    const QV* Qtk = reinterpret_cast<const QV*>(Qt + kr * ldP);
+    const QV* Qxb = reinterpret_cast<const QV*>(Q + xb * ldP);
+    const QV* Qtxb = reinterpret_cast<const QV*>(Qt + xb * ldP);
+    int A1 = 0, A2 = 0, B1 = 0, B2 = 0;
+    if (sym) {
+      for (int c = lg; c < nc; c += G) {
+        A1 = C::dot(Fx[c], Qk[c], A1);
+        B1 = C::dot(Fk[c], Qxb[c], B1);
+      }
+    } else {
+      for (int c = lg; c < nc; c += G) {
+        A1 = C::dot(Fx[c], Qk[c], A1);
+        A2 = C::dot(Ftx[c], Qtk[c], A2);
+        B1 = C::dot(Fk[c], Qxb[c], B1);
+        B2 = C::dot(Ftk[c], Qtxb[c], B2);
+      }
+    }
+    // each of A1 + A2 and B1 + B2 is at most 2 n 2^15 2^7 < 2^31 in magnitude
+    int A = A1 + A2, B = B1 + B2;
+    for (int o = G >> 1; o > 0; o >>= 1) {
+      A += __shfl_xor_sync(gmask, A, o);
+      B += __shfl_xor_sync(gmask, B, o);
+    }
+    if (lg != 0) continue;
+    // 2x2 blocks of F and Q at {r, s}
+    const int fRR = F[r * ldF + r], fRS = F[r * ldF + s];
+    const int fSR = F[s * ldF + r], fSS = F[s * ldF + s];
+    const int qRR = Q[r * ldP + r], qRS = Q[r * ldP + s];
+    const int qSR = Q[s * ldP + r], qSS = Q[s * ldP + s];
+    // column-exchange coefficients: (F[x][r]-F[x][s]), (F[r][x]-F[s][x]),
+    // (Q[xb][s]-Q[xb][r]), (Q[s][xb]-Q[r][xb])
+    const int fx_rs = xi ? fSR - fSS : fRR - fRS;
+    const int frs_x = xi ? fRS - fSS : fRR - fSR;
+    const int qxb_sr = xi ? qRS - qRR : qSS - qSR;
+    const int qsr_xb = xi ? qSR - qRR : qSS - qRS;
+    if (gtask) {
+      const int c1 = fx_rs * qxb_sr, c2 = frs_x * qsr_xb;
+      gn[x] = sym ? (DT)2 * ((DT)A + (DT)c1) : (DT)A + (DT)c1 + (DT)c2;
+      continue;
+    }
+    const int Frk = F[r * ldF + k], Fsk = F[s * ldF + k];
+    const int Fkr = Ft[r * ldF + k], Fks = Ft[s * ldF + k];
+    const int Qrk = Q[r * ldP + k], Qsk = Q[s * ldP + k];
+    const int Qkr = Qt[r * ldP + k], Qks = Qt[s * ldP + k];
+    const int Fkk = F[k * ldF + k], Qkk = Q[k * ldP + k];
+    const int a = Frk - Fsk, b = Qrk - Qsk, c = Fkr - Fks, e = Qkr - Qks;
+    const DT gk = gc[k] - (DT)(a * b) - (DT)(c * e);
+    const int fxx = xi ? fSS : fRR;  // F[x][x]
+    const int pxx = xi ? qRR : qSS;  // P'[x][x] = Q[xb][xb]
+    const int fxk = xi ? Fsk : Frk;  // F[x][k]
+    const int fkx = xi ? Fks : Fkr;  // F[k][x]
+    const int pxk = xi ? Qrk : Qsk;  // P'[x][k] = Q[xb][k]
+    const int pkx = xi ? Qkr : Qks;  // P'[k][x] = Q[k][xb]
+    const int corr = (fxx - fxk - fkx + Fkk) * (pxx - pxk - pkx + Qkk);
+    const int sig = -fx_rs * e - frs_x * b + qxb_sr * c + qsr_xb * a;
+    const DT cross = sym ? (DT)2 * ((DT)A + (DT)B) : (DT)A + (DT)B;
+    S.R[xi * n + k] = cross + (DT)sig - gk + (DT)corr;
+    if (xi == 0) {
+      S.vec[k] = make_int4(a, b, c, e);
+      gn[k] = gk;
+    }
+  }
+}
+
+// Exchange rows and columns r, s of P (and P^T) and p[r], p[s].
+template <int NT>
+__device__ __forceinline__ void swap_rs(int8_t* P, int8_t* Pt, int32_t* perm, int n, int ldP,
+                                        bool symD, int r, int s) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    const int32_t t = perm[r];
+    perm[r] = perm[s];
+    perm[s] = t;
+  }
   for (int j = tid; j < n; j += NT) {
     if (j != r && j != s) {
-      int8_t* Pr = S.P + r * ldP;
-      int8_t* Ps = S.P + s * ldP;
+      int8_t* Pr = P + r * ldP;
+      int8_t* Ps = P + s * ldP;
       int8_t t = Pr[j]; Pr[j] = Ps[j]; Ps[j] = t;
-      int8_t* Pj = S.P + j * ldP;
+      int8_t* Pj = P + j * ldP;
       t = Pj[r]; Pj[r] = Pj[s]; Pj[s] = t;
       if (!symD) {
-        int8_t* Qr = S.Pt + r * ldP;
-        int8_t* Qs = S.Pt + s * ldP;
+        int8_t* Qr = Pt + r * ldP;
+        int8_t* Qs = Pt + s * ldP;
         t = Qr[j]; Qr[j] = Qs[j]; Qs[j] = t;
-        int8_t* Qj = S.Pt + j * ldP;
+        int8_t* Qj = Pt + j * ldP;
         t = Qj[r]; Qj[r] = Qj[s]; Qj[s] = t;
       }
     } else if (j == r) {
-      int8_t* Pr = S.P + r * ldP;
-      int8_t* Ps = S.P + s * ldP;
+      int8_t* Pr = P + r * ldP;
+      int8_t* Ps = P + s * ldP;
       const int8_t rr = Pr[r], rs = Pr[s], sr = Ps[r], ss = Ps[s];
       Pr[r] = ss; Pr[s] = sr; Ps[r] = rs; Ps[s] = rr;
       if (!symD) {
-        int8_t* Qr = S.Pt + r * ldP;
-        int8_t* Qs = S.Pt + s * ldP;
+        int8_t* Qr = Pt + r * ldP;
+        int8_t* Qs = Pt + s * ldP;
         const int8_t qrr = Qr[r], qrs = Qr[s], qsr = Qs[r], qss = Qs[s];
         Qr[r] = qss; Qr[s] = qsr; Qs[r] = qrs; Qs[s] = qrr;
       }
     }
   }
-  __syncthreads();
-
-  if (copy_best)
-    for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
-
-  // O(1)-update vectors from F and P'.
-  {
-    const int16_t* Fr = S.F + r * ldF;
-    const int16_t* Fs = S.F + s * ldF;
-    const int8_t* Pr = S.P + r * ldP;
-    const int8_t* Ps = S.P + s * ldP;
-    const int16_t* Ftr = S.Ft + r * ldF;
-    const int16_t* Fts = S.Ft + s * ldF;
-    const int8_t* Ptr = S.Pt + r * ldP;
-    const int8_t* Pts = S.Pt + s * ldP;
-    for (int x = tid; x < n; x += NT) {
-      const int a = (int)Fr[x] - (int)Fs[x];
-      const int b = (int)Ps[x] - (int)Pr[x];
-      const int c = sym ? a : (int)Ftr[x] - (int)Fts[x];
-      const int e = sym ? b : (int)Pts[x] - (int)Ptr[x];
-      S.vec[x] = make_int4(a, b, c, e);
-    }
-  }
-
-  // Eq. 2 recomputed for the pairs {r, k} (row 0 of R) and {s, k} (row 1),
-  // k outside {r, s}; one 8-lane group per pair.
-  {
-    const int lane8 = tid & (kGroup - 1);
-    const int group = tid / kGroup;
-    constexpr int NG = NT / kGroup;
-    const unsigned gmask = 0xffu << (threadIdx.x & 31 & ~(kGroup - 1));
-    for (int q = group; q < 2 * n; q += NG) {
-      const int xi = q >= n ? 1 : 0;
-      const int k = q - xi * n;
-      if (k == r || k == s) continue;
-      const int x = xi ? s : r;
-      const int16_t* Fx = S.F + x * ldF;
-      const int16_t* Fk = S.F + k * ldF;
-      const int8_t* Px = S.P + x * ldP;
-      const int8_t* Pk = S.P + k * ldP;
-      DT acc = 0;
-      if (sym) {
-        int part = 0;
-        for (int j = lane8; j < n; j += kGroup) {
-          const int t1 = ((int)Fx[j] - (int)Fk[j]) * ((int)Pk[j] - (int)Px[j]);
-          part += (j == x || j == k) ? 0 : t1;
-        }
-        acc = (DT)2 * (DT)part;
-      } else {
-        const int16_t* Ftx = S.Ft + x * ldF;
-        const int16_t* Ftk = S.Ft + k * ldF;
-        const int8_t* Ptx = S.Pt + x * ldP;
-        const int8_t* Ptk = S.Pt + k * ldP;
-        for (int j = lane8; j < n; j += kGroup) {
-          const int t1 = ((int)Fx[j] - (int)Fk[j]) * ((int)Pk[j] - (int)Px[j]);
-          const int t2 = ((int)Ftx[j] - (int)Ftk[j]) * ((int)Ptk[j] - (int)Ptx[j]);
-          acc += (j == x || j == k) ? (DT)0 : (DT)t1 + (DT)t2;
-        }
-      }
-#pragma unroll
-      for (int o = kGroup / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o);
-      if (lane8 == 0) {
-        const int fixed = ((int)Fx[k] - (int)Fk[x]) * ((int)Pk[x] - (int)Px[k]);
-        const int diag = ((int)Fx[x] - (int)Fk[k]) * ((int)Pk[k] - (int)Px[x]);
-        S.R[xi * n + k] = acc + (DT)fixed + (DT)diag;
-      }
-    }
-  }
-  __syncthreads();
-}
-
-// New delta of an owned pair after move (r, s) (vectors and rows ready).
-template <typename DT>
-__device__ __forceinline__ DT updated_delta(const WalkSmem<DT>& S, int n, DT d, uint32_t key,
-                                            uint32_t rs, int r, int s) {
-  const int u = (int)(key >> 8), v = (int)(key & 0xffu);
-  if (key == rs) return -d;
-  if (u == r || v == r) return S.R[u == r ? v : u];
-  if (u == s || v == s) return S.R[n + (u == s ? v : u)];
-  const int4 A = S.vec[u], B = S.vec[v];
-  return d + (DT)((A.x - B.x) * (A.y - B.y) + (A.z - B.z) * (A.w - B.w));
 }
 
 // ---------------------------------------------------------------------------
@@ -325,21 +416,25 @@ __device__ __forceinline__ DT updated_delta(const WalkSmem<DT>& S, int n, DT d, 
 // ---------------------------------------------------------------------------
 constexpr int min_blocks(int nt) { return nt <= 128 ? 4 : nt <= 256 ? 2 : 1; }
 
-template <typename DT, int NT, int MAXPT>
+template <typename DT, typename FE, int NT, int MAXPT>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n = a.n, ldF = a.ldF, ldP = a.ldP, tid = threadIdx.x;
+  const int n = a.n, ldF = a.ldF, ldP = a.ldP, tid = threadIdx.x, G = a.group;
   const int T = n * (n - 1) / 2;
   const bool sym = a.symF && a.symD;
-  const SmemLayout L = smem_layout(n, ldF, ldP, a.symF, a.symD, (int)sizeof(DT));
-  WalkSmem<DT> S;
-  S.F = reinterpret_cast<int16_t*>(smem + L.offF);
-  S.Ft = a.symF ? S.F : reinterpret_cast<int16_t*>(smem + L.offFt);
+  const bool warp0 = tid < 32;
+  const SmemLayout L =
+      smem_layout(n, ldF, (int)sizeof(FE), ldP, a.symF, a.symD, (int)sizeof(DT));
+  WalkSmem<DT, FE> S;
+  S.F = reinterpret_cast<FE*>(smem + L.offF);
+  S.Ft = a.symF ? S.F : reinterpret_cast<FE*>(smem + L.offFt);
   S.P = reinterpret_cast<int8_t*>(smem + L.offP);
   S.Pt = a.symD ? S.P : reinterpret_cast<int8_t*>(smem + L.offPt);
   S.tabu = reinterpret_cast<int32_t*>(smem + L.offTabu);
   S.vec = reinterpret_cast<int4*>(smem + L.offVec);
   S.R = reinterpret_cast<DT*>(smem + L.offR);
+  S.g0 = reinterpret_cast<DT*>(smem + L.offG0);
+  S.g1 = reinterpret_cast<DT*>(smem + L.offG1);
   S.perm = reinterpret_cast<int32_t*>(smem + L.offPerm);
   S.best = reinterpret_cast<int32_t*>(smem + L.offBest);
   S.redD = reinterpret_cast<DT*>(smem + L.offRedD);
@@ -369,9 +464,10 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
   }
 #define QAP_KEY(i) ((kp[(i) / 2] >> (16 * ((i) & 1))) & 0xffffu)
 
-  // F (and F^T) once per CTA: rows are whole 16-byte vectors.
+  // F (and F^T) once per CTA (rows are whole 16-byte vectors, zero padded);
+  // P (and P^T) zeroed once so their padding columns stay zero.
   {
-    const int nvec = n * ldF * 2 / 16;
+    const int nvec = n * ldF * (int)sizeof(FE) / 16;
     const int4* gF = reinterpret_cast<const int4*>(a.F);
     int4* sF = reinterpret_cast<int4*>(S.F);
     for (int i = tid; i < nvec; i += NT) sF[i] = gF[i];
@@ -380,7 +476,15 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
       int4* sFt = reinterpret_cast<int4*>(S.Ft);
       for (int i = tid; i < nvec; i += NT) sFt[i] = gFt[i];
     }
+    const int pvec = n * ldP / 16;
+    int4* sP = reinterpret_cast<int4*>(S.P);
+    for (int i = tid; i < pvec; i += NT) sP[i] = make_int4(0, 0, 0, 0);
+    if (!a.symD) {
+      int4* sPt = reinterpret_cast<int4*>(S.Pt);
+      for (int i = tid; i < pvec; i += NT) sPt[i] = make_int4(0, 0, 0, 0);
+    }
   }
+  __syncthreads();
 
   for (int w = blockIdx.x; w < a.walks; w += gridDim.x) {
     const int wi = a.walk_offset + w;
@@ -414,54 +518,93 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
     for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
     __syncthreads();
 
-    // Eq. 1.
+    // Eq. 1, g, and the initial deltas of the owned pairs (Eq. 2, O(n) each).
     int64_t c0 = 0;
     for (int c = tid; c < n * n; c += NT) {
       const int i = c / n, j = c - (c / n) * n;
       c0 += (int64_t)S.F[i * ldF + j] * (int64_t)S.P[i * ldP + j];
     }
     c0 = block_sum<NT>(c0, S.sum);
-
-    // Initial deltas of the owned pairs (Eq. 2, O(n) each) and tabu table.
+    compute_g<DT, FE, NT>(S, S.g0, n, ldF, ldP, sym, G);
     DT dl[MAXPT];
 #pragma unroll
     for (int i = 0; i < MAXPT; ++i) {
       dl[i] = 0;
       if (QAP_KEY(i) != kNoPair) {
-        dl[i] = delta_serial<DT>(S, n, ldF, ldP, sym, (int)(QAP_KEY(i) >> 8), (int)(QAP_KEY(i) & 0xffu));
+        dl[i] = delta_serial<DT, FE>(S, n, ldF, ldP, sym, (int)(QAP_KEY(i) >> 8),
+                                     (int)(QAP_KEY(i) & 0xffu));
         S.tabu[tid + i * NT] = 0;
       }
     }
 
     DT cur = (DT)c0;
+    DT* gc = S.g0;
+    DT* gn = S.g1;
     uint64_t h = 14695981039346656037ull, dh = h;
     int dmoves = 0;
+
+    // Owners' pass after move (r, s): new deltas, then the scan for the next
+    // iteration `nit` (tabu phase) or the next descent step.  Branch-free per
+    // slot so the shared-memory loads of all slots are in flight together;
+    // slot indexes are clamped in range where a slot holds no pair.
+    auto update_and_scan = [&](uint32_t rs, int r, int s, bool tabu, int nit, int stamp,
+                               DT ncur, DT nbest, DT& bd, uint32_t& bk) {
+      const DT gr = gn[r], gs = gn[s];
+      bd = DeltaMax<DT>::v;
+      bk = kNoMove;
+#pragma unroll
+      for (int i = 0; i < MAXPT; ++i) {
+        if (i * NT + (tid & ~31) >= T) break;  // whole warp past the last pair
+        const uint32_t k16 = QAP_KEY(i);
+        const bool valid = k16 != kNoPair;
+        const int u = valid ? (int)(k16 >> 8) : 0;
+        const int v = valid ? (int)(k16 & 0xffu) : 0;
+        const int q = valid ? tid + i * NT : 0;
+        const int4 A = S.vec[u], B = S.vec[v];
+        const bool tr = (u == r) | (v == r);
+        const bool ts = (u == s) | (v == s);
+        const int oth = (tr | ts) ? (u ^ v ^ (tr ? r : s)) : 0;
+        const DT rv = S.R[(tr ? 0 : n) + oth];
+        DT d = dl[i];
+        const DT o1 = d + (DT)((A.x - B.x) * (A.y - B.y) + (A.z - B.z) * (A.w - B.w));
+        d = (k16 == rs) ? -d : (tr | ts) ? rv - (tr ? gr : gs) : o1;
+        if (valid) dl[i] = d;
+        if (tabu && k16 == rs) S.tabu[q] = stamp;
+        const bool adm =
+            !tabu || S.tabu[q] <= nit || (a.aspiration && ncur + d < nbest);
+        if (valid && adm && d < bd) {
+          bd = d;
+          bk = k16;
+        }
+      }
+    };
 
     // ---- 2opt descent (Section 4.1): best move while it improves.
     if (a.descend) {
       // A descent strictly lowers the cost at every move, so it ends; the
       // cap only bounds the kernel's run time on any input.
       const int cap = a.max_descent >= 0 ? a.max_descent : kDescentCap;
+      DT bd = DeltaMax<DT>::v;
+      uint32_t bk = kNoMove;
+#pragma unroll
+      for (int i = 0; i < MAXPT; ++i)
+        if (QAP_KEY(i) != kNoPair && dl[i] < bd) {
+          bd = dl[i];
+          bk = QAP_KEY(i);
+        }
       for (;;) {
         if (dmoves >= cap) break;
-        DT bd = DeltaMax<DT>::v;
-        uint32_t bk = kNoMove;
-#pragma unroll
-        for (int i = 0; i < MAXPT; ++i)
-          if (QAP_KEY(i) != kNoPair && dl[i] < bd) {
-            bd = dl[i];
-            bk = QAP_KEY(i);
-          }
         block_argmin<DT, NT>(bd, bk, S.redD, S.redK);
         if (bk == kNoMove || bd >= 0) break;
         const int r = (int)(bk >> 8), s = (int)(bk & 0xffu);
         cur += bd;
         ++dmoves;
-        dh = fnv_step(dh, r, s);
-        apply_move<DT, NT>(S, n, ldF, ldP, a.symF, a.symD, r, s, false);
-#pragma unroll
-        for (int i = 0; i < MAXPT; ++i)
-          if (QAP_KEY(i) != kNoPair) dl[i] = updated_delta<DT>(S, n, dl[i], QAP_KEY(i), bk, r, s);
+        if (warp0) dh = fnv_step(dh, r, s);
+        phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
+        __syncthreads();
+        update_and_scan(bk, r, s, false, 0, 0, cur, cur, bd, bk);
+        swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, a.symD, r, s);
+        DT* t = gc; gc = gn; gn = t;
       }
       __syncthreads();
       for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
@@ -470,20 +613,29 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
     // ---- tabu search (Sections 4.3, 4.4).
     DT best = cur;
     int best_iter = 0, status = 0, done = 0;
-    for (int it = 1; it <= a.iters; ++it) {
-      DT bd = DeltaMax<DT>::v;
-      uint32_t bk = kNoMove;
+    bool copy_pending = false;
+    int tenure = 0, tleft = 1;  // period > 0: a new tenure when tleft reaches 0
+    uint32_t tdraw = 0;
+    DT bd = DeltaMax<DT>::v;
+    uint32_t bk = kNoMove;
+    if (a.iters > 0) {
 #pragma unroll
       for (int i = 0; i < MAXPT; ++i) {
         if (QAP_KEY(i) == kNoPair) continue;
         const DT d = dl[i];
-        const bool adm = S.tabu[tid + i * NT] <= it || (a.aspiration && cur + d < best);
+        const bool adm = S.tabu[tid + i * NT] <= 1 || (a.aspiration && cur + d < best);
         if (adm && d < bd) {
           bd = d;
           bk = QAP_KEY(i);
         }
       }
+    }
+    for (int it = 1; it <= a.iters; ++it) {
       block_argmin<DT, NT>(bd, bk, S.redD, S.redK);
+      if (copy_pending) {  // p after the previous iteration's move
+        for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
+        copy_pending = false;
+      }
       if (bk == kNoMove) {
         status = 1;
         break;
@@ -491,25 +643,38 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
       const int r = (int)(bk >> 8), s = (int)(bk & 0xffu);
       cur += bd;
       done = it;
-      h = fnv_step(h, r, s);
-      const bool improved = cur < best;
-      if (improved) {
+      if (warp0) h = fnv_step(h, r, s);
+      if (cur < best) {
         best = cur;
         best_iter = it;
+        copy_pending = true;
       }
+      if (a.period > 0 && --tleft == 0) {  // it = 1, period + 1, ...
+        const uint32_t x = walk_draw(a.seed, wid, 1u, tdraw++);
+        tenure = a.tmin + (int)below(x, (uint32_t)(a.tmax - a.tmin + 1));
+        tleft = a.period;
+      }
+      phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
+      __syncthreads();
+      int stamp = it + tenure;
+      if (a.period == 0) {
+        // the paper's rule: a fresh tenure per move, drawn by the owner only
+        bool owner = false;
 #pragma unroll
-      for (int i = 0; i < MAXPT; ++i) {
-        if (QAP_KEY(i) == bk) {
-          const uint32_t k = a.period > 0 ? (uint32_t)((it - 1) / a.period) : (uint32_t)(it - 1);
-          const uint32_t x = walk_draw(a.seed, wid, 1u, k);
-          S.tabu[tid + i * NT] = it + a.tmin + (int)below(x, (uint32_t)(a.tmax - a.tmin + 1));
+        for (int i = 0; i < MAXPT; ++i) owner |= (QAP_KEY(i) == bk);
+        if (owner) {
+          const uint32_t x = walk_draw(a.seed, wid, 1u, (uint32_t)(it - 1));
+          stamp = it + a.tmin + (int)below(x, (uint32_t)(a.tmax - a.tmin + 1));
         }
       }
-      apply_move<DT, NT>(S, n, ldF, ldP, a.symF, a.symD, r, s, improved);
-#pragma unroll
-      for (int i = 0; i < MAXPT; ++i)
-        if (QAP_KEY(i) != kNoPair) dl[i] = updated_delta<DT>(S, n, dl[i], QAP_KEY(i), bk, r, s);
+      const uint32_t rs = bk;
+      update_and_scan(rs, r, s, true, it + 1, stamp, cur, best, bd, bk);
+      swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, a.symD, r, s);
+      DT* t = gc; gc = gn; gn = t;
     }
+    __syncthreads();
+    if (copy_pending)
+      for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
     __syncthreads();
 
     // ---- outputs
@@ -535,8 +700,8 @@ using WalkKernelFn = void (*)(const WalkArgs);
 // ---------------------------------------------------------------------------
 // Eq. 1 for a batch of permutations: one CTA per permutation.
 // ---------------------------------------------------------------------------
-template <int NT>
-__global__ void __launch_bounds__(NT) cost_kernel(const int16_t* __restrict__ F, int ldF,
+template <typename FE, int NT>
+__global__ void __launch_bounds__(NT) cost_kernel(const FE* __restrict__ F, int ldF,
                                                  const int8_t* __restrict__ D, int n,
                                                  const int32_t* __restrict__ p, int count,
                                                  int64_t* __restrict__ out) {
