@@ -72,26 +72,32 @@ namespace {
 using KernelFn = qapk::WalkKernelFn;
 
 // Register plans (threads per walk, pair slots per thread) compiled into the
-// library.  The automatic choice takes the fewest threads that keep at most
-// six pairs per thread, then the fewest slots that hold them all.
+// library.  A plan fits n when its row segments (qapk::row_segments) number
+// at most its threads.  The automatic choice takes the fewest threads that fit
+// with at most eight slots, else the fewest threads that fit at all; for a
+// given thread count the fewest slots that fit.
 const Plan kPlans[] = {{128, 4},  {128, 12}, {256, 6},  {256, 8},   {512, 4},
-                       {512, 8},  {512, 12}, {1024, 8}, {1024, 12}, {1024, 16}};
+                       {512, 8},  {512, 12}, {1024, 8}, {1024, 12}, {1024, 16},
+                       {1024, 20}};
 
-bool choose_plan(int n, int threads, Plan* out) {
-  const int T = n * (n - 1) / 2;
-  int nt = threads;
-  if (nt == 0) {
-    nt = 1024;
-    for (int c : {128, 256, 512, 1024})
-      if (T <= 6 * c) {
-        nt = c;
-        break;
-      }
-  }
+bool plan_for(int n, int nt, Plan* out) {
   for (const Plan& p : kPlans)
-    if (p.nt == nt && T <= p.nt * p.maxpt) {
+    if (p.nt == nt && qapk::row_segments(n, p.maxpt) <= nt) {
       *out = p;
       return true;
+    }
+  return false;
+}
+
+bool choose_plan(int n, int threads, Plan* out) {
+  if (threads != 0) return plan_for(n, threads, out);
+  for (int pass = 0; pass < 2; ++pass)
+    for (int nt : {128, 256, 512, 1024}) {
+      Plan p;
+      if (plan_for(n, nt, &p) && (pass == 1 || p.maxpt <= 8)) {
+        *out = p;
+        return true;
+      }
     }
   return false;
 }
@@ -144,7 +150,7 @@ qap_status plan_launch(qap_ctx* ctx, const qap_search_params* p, Launch* L) {
   if (!L->fn) return QAP_EUNSUPPORTED;
   const qapk::SmemLayout S =
       qapk::smem_layout(ctx->n, ctx->ldF, ctx->fbytes, ctx->ldP, ctx->symF, ctx->symD,
-                        ctx->dbytes);
+                        ctx->dbytes, L->plan.nt * L->plan.maxpt);
   L->smem = S.bytes;
   if (L->smem > ctx->smem_optin) return QAP_EUNSUPPORTED;
   qap_status st = prepare_kernel(L->fn, L->smem);
@@ -156,10 +162,10 @@ qap_status plan_launch(qap_ctx* ctx, const qap_search_params* p, Launch* L) {
   L->ctas_per_sm = occ;
   L->grid = std::min(p->starts, occ * ctx->sms);
   // widest power-of-two group (<= 8 lanes, <= the row chunks) that still
-  // gives every (row, index) task of phase X its own group
+  // gives every index of phase X its own group
   const int nc = (ctx->n + 16 / ctx->fbytes - 1) / (16 / ctx->fbytes);
   L->group = 8;
-  while (L->group > 1 && (L->plan.nt / L->group < 2 * ctx->n || L->group > nc)) L->group >>= 1;
+  while (L->group > 1 && (L->plan.nt / L->group < ctx->n || L->group > nc)) L->group >>= 1;
   return QAP_OK;
 }
 
@@ -269,7 +275,9 @@ qap_status qap_create(const int64_t* F, const int64_t* D, int32_t n, uint32_t fl
   c->dbytes = ((flags & QAP_FORCE_INT64) || bound > (int64_t)INT_MAX - 1) ? 8 : 4;
   // int8 flows (dp4a rows) when they fit and deltas are int32; else int16
   c->fbytes = (mF <= 127 && c->dbytes == 4) ? 1 : 2;
-  c->ldF = round_up(n, 16 / c->fbytes);
+  // F rows: an odd number of 16-byte chunks, so rows read side by side by
+  // the lanes of a warp fall in different banks
+  c->ldF = (16 / c->fbytes) * (((n * c->fbytes + 15) / 16) | 1);
   // P rows: an odd number of 16-byte chunks, so the column exchanges of a
   // move hit 8 different banks per 32 rows instead of 2
   c->ldP = 16 * (((n + 15) / 16) | 1);

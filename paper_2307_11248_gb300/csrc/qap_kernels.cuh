@@ -8,9 +8,8 @@
 //                   pair); the O(1)-update vectors; two recomputed delta
 //                   rows; g[k] = sum_j F[k][j]P[k][j] + F[j][k]P[j][k]
 //                   (double-buffered); p and the best permutation.
-//   registers       the delta of every pair the thread owns (thread t owns
-//                   pairs t, t + NT, t + 2 NT, ... of the lexicographic pair
-//                   order) and the packed (r << 8 | s) key of each.
+//   registers       the delta of every pair the thread owns: a segment of
+//                   at most MAXPT consecutive pairs (u, v) of one row u.
 //
 // One tabu iteration, move (r, s) already chosen, has two barriers:
 //   phase X  (reads the pre-move P, called Q below)  one task per index k:
@@ -47,7 +46,6 @@ namespace qapk {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kNoMove = 0xffffffffu;
-constexpr uint32_t kNoPair = 0xffffu;     // packed-key slot without a pair
 constexpr int kDescentCap = 1 << 20;      // 2opt moves when no cap is given
 
 struct WalkArgs {
@@ -87,15 +85,14 @@ struct SmemLayout {
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
 __host__ __device__ inline SmemLayout smem_layout(int n, int ldF, int fbytes, int ldP, int symF,
-                                                  int symD, int dbytes) {
+                                                  int symD, int dbytes, int slots) {
   SmemLayout L;
-  const int T = n * (n - 1) / 2;
   int o = 0;
   L.offF = o;    o = align16(o + n * ldF * fbytes);
   L.offFt = o;   o = symF ? o : align16(o + n * ldF * fbytes);
   L.offP = o;    o = align16(o + n * ldP);
   L.offPt = o;   o = symD ? o : align16(o + n * ldP);
-  L.offTabu = o; o = align16(o + T * 4);
+  L.offTabu = o; o = align16(o + slots * 4);
   L.offVec = o;  o = align16(o + n * 16);
   L.offR = o;    o = align16(o + 2 * n * dbytes);
   L.offG0 = o;   o = align16(o + n * dbytes);
@@ -139,6 +136,39 @@ template <> struct Chunk<int16_t> {
     acc = __dp2a_hi(f.y, q.x, acc);
     acc = __dp2a_lo(f.z, q.y, acc);
     return __dp2a_hi(f.w, q.y, acc);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// O(1)-update vectors (a, b, c, e) of one index: four int16 in 8 bytes when
+// the flows are int8 (every entry then lies in [-255, 255]), else four int32
+// ---------------------------------------------------------------------------
+template <typename FE> struct VecOps;
+
+template <> struct VecOps<int8_t> {
+  using V = int2;
+  __device__ __forceinline__ static V pack(int a, int b, int c, int e) {
+    return make_int2((int)(((uint32_t)a & 0xffffu) | ((uint32_t)b << 16)),
+                     (int)(((uint32_t)c & 0xffffu) | ((uint32_t)e << 16)));
+  }
+  __device__ __forceinline__ static void unpack(const V w, int& a, int& b, int& c, int& e) {
+    a = (int)(short)(w.x & 0xffff);
+    b = w.x >> 16;
+    c = (int)(short)(w.y & 0xffff);
+    e = w.y >> 16;
+  }
+};
+
+template <> struct VecOps<int16_t> {
+  using V = int4;
+  __device__ __forceinline__ static V pack(int a, int b, int c, int e) {
+    return make_int4(a, b, c, e);
+  }
+  __device__ __forceinline__ static void unpack(const V w, int& a, int& b, int& c, int& e) {
+    a = w.x;
+    b = w.y;
+    c = w.z;
+    e = w.w;
   }
 };
 
@@ -208,7 +238,7 @@ struct WalkSmem {
   int8_t* P;
   int8_t* Pt;
   int32_t* tabu;
-  int4* vec;
+  void* vec;  // VecOps<FE>::V per index
   DT* R;
   DT* g0;
   DT* g1;
@@ -274,18 +304,19 @@ __device__ __forceinline__ void compute_g(const WalkSmem<DT, FE>& S, DT* g, int 
   }
 }
 
-// Phase X of move (r, s): see the file header.  One task per (row xi, index
-// k), xi = 0 for the pairs {r, k} and 1 for {s, k}; G lanes per task split the
-// row chunks.  The task k = x of row xi computes g'[x] instead, the task
-// k = xb (the other index of the move) has nothing to do.  Reads Q = P before
-// the move and gc = g of the pre-move state; writes vec, R (rows {r,k} and
-// {s,k} without their -g'[x] term) and gn = g after the move.
+// Phase X of move (r, s): see the file header.  One task per index k, G
+// lanes per task splitting the row chunks; the k-row chunks serve both rows
+// {r, k} and {s, k}.  Tasks k = r and k = s compute g'[r] and g'[s].  After a
+// reduce-scatter over the group, lane 0 finishes row {r, k} and lane 1 row
+// {s, k} (lane 0 both when G = 1).  Reads Q = P before the move and gc = g of
+// the pre-move state; writes vec, R (without the -g'[x] term) and gn.
 template <typename DT, typename FE, int NT>
 __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc, DT* gn, int n,
                                         int ldF, int ldP, bool sym, int G, int r, int s) {
   using C = Chunk<FE>;
   using FV = typename C::FV;
   using QV = typename C::QV;
+  using VO = VecOps<FE>;
   const int lg = threadIdx.x & (G - 1);
   const int grp = threadIdx.x / G;
   const int NG = NT / G;
@@ -295,57 +326,74 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
   const int8_t* Q = S.P;
   const FE* Ft = S.Ft;
   const int8_t* Qt = S.Pt;
-  for (int t = grp; t < 2 * n; t += NG) {
-    const int xi = t & 1, k = t >> 1;
-    const int x = xi ? s : r, xb = xi ? r : s;
-    if (k == xb) continue;  // uniform per group
-    const bool gtask = (k == x);
-    // k-task: A = F[x].Q[k] + F^T[x].Q^T[k], B = F[k].Q[xb] + F^T[k].Q^T[xb]
-    // g-task: the row paired with x is xb, so A = F[x].Q[xb] + F^T[x].Q^T[xb]
-    const int kr = gtask ? xb : k;
-    const FV* Fx = reinterpret_cast<const FV*>(F + x * ldF);
-    const FV* Ftx = reinterpret_cast<const FV*>(Ft + x * ldF);
-    const FV* Fk = reinterpret_cast<const FV*>(F + kr * ldF);
-    const FV* Ftk = reinterpret_cast<const FV*>(Ft + kr * ldF);
-    const QV* Qk = reinterpret_cast<const QV*>(Q + kr * ldP);
-    const QV* Qtk = reinterpret_cast<const QV*>(Qt + kr * ldP);
-    const QV* Qxb = reinterpret_cast<const QV*>(Q + xb * ldP);
-    const QV* Qtxb = reinterpret_cast<const QV*>(Qt + xb * ldP);
-    int A1 = 0, A2 = 0, B1 = 0, B2 = 0;
+  const FV* Fr = reinterpret_cast<const FV*>(F + r * ldF);
+  const FV* Fs = reinterpret_cast<const FV*>(F + s * ldF);
+  const FV* Ftr = reinterpret_cast<const FV*>(Ft + r * ldF);
+  const FV* Fts = reinterpret_cast<const FV*>(Ft + s * ldF);
+  const QV* Qr = reinterpret_cast<const QV*>(Q + r * ldP);
+  const QV* Qs = reinterpret_cast<const QV*>(Q + s * ldP);
+  const QV* Qtr = reinterpret_cast<const QV*>(Qt + r * ldP);
+  const QV* Qts = reinterpret_cast<const QV*>(Qt + s * ldP);
+  for (int k = grp; k < n; k += NG) {
+    const bool gt = (k == r) | (k == s);
+    // k-task: Ar = F[r].Q[k] + F^T[r].Q^T[k]   Br = F[k].Q[s] + F^T[k].Q^T[s]
+    //         As = F[s].Q[k] + F^T[s].Q^T[k]   Bs = F[k].Q[r] + F^T[k].Q^T[r]
+    // g-task k = r: Ar with the row s in place of k; k = s: As with row r
+    const int kq = gt ? (k == r ? s : r) : k;
+    const FV* Fk = reinterpret_cast<const FV*>(F + kq * ldF);
+    const FV* Ftk = reinterpret_cast<const FV*>(Ft + kq * ldF);
+    const QV* Qk = reinterpret_cast<const QV*>(Q + kq * ldP);
+    const QV* Qtk = reinterpret_cast<const QV*>(Qt + kq * ldP);
+    int Ar = 0, Br = 0, As = 0, Bs = 0;
     if (sym) {
       for (int c = lg; c < nc; c += G) {
-        A1 = C::dot(Fx[c], Qk[c], A1);
-        B1 = C::dot(Fk[c], Qxb[c], B1);
+        const FV fk = Fk[c];
+        const QV qk = Qk[c];
+        Ar = C::dot(Fr[c], qk, Ar);
+        As = C::dot(Fs[c], qk, As);
+        Br = C::dot(fk, Qs[c], Br);
+        Bs = C::dot(fk, Qr[c], Bs);
       }
     } else {
       for (int c = lg; c < nc; c += G) {
-        A1 = C::dot(Fx[c], Qk[c], A1);
-        A2 = C::dot(Ftx[c], Qtk[c], A2);
-        B1 = C::dot(Fk[c], Qxb[c], B1);
-        B2 = C::dot(Ftk[c], Qtxb[c], B2);
+        const FV fk = Fk[c], ftk = Ftk[c];
+        const QV qk = Qk[c], qtk = Qtk[c];
+        Ar = C::dot(Fr[c], qk, Ar);
+        Ar = C::dot(Ftr[c], qtk, Ar);
+        As = C::dot(Fs[c], qk, As);
+        As = C::dot(Fts[c], qtk, As);
+        Br = C::dot(fk, Qs[c], Br);
+        Br = C::dot(ftk, Qts[c], Br);
+        Bs = C::dot(fk, Qr[c], Bs);
+        Bs = C::dot(ftk, Qtr[c], Bs);
       }
     }
-    // each of A1 + A2 and B1 + B2 is at most 2 n 2^15 2^7 < 2^31 in magnitude
-    int A = A1 + A2, B = B1 + B2;
-    for (int o = G >> 1; o > 0; o >>= 1) {
-      A += __shfl_xor_sync(gmask, A, o);
-      B += __shfl_xor_sync(gmask, B, o);
+    // reduce-scatter: even lanes gather (Ar, Br), odd lanes (As, Bs)
+    const bool odd = lg & 1;
+    int A = odd ? As : Ar, B = odd ? Bs : Br;
+    if (G > 1) {
+      A += __shfl_xor_sync(gmask, odd ? Ar : As, 1);
+      B += __shfl_xor_sync(gmask, odd ? Br : Bs, 1);
+      for (int o = 2; o < G; o <<= 1) {
+        A += __shfl_xor_sync(gmask, A, o);
+        B += __shfl_xor_sync(gmask, B, o);
+      }
     }
-    if (lg != 0) continue;
+    if (lg > 1) continue;
     // 2x2 blocks of F and Q at {r, s}
     const int fRR = F[r * ldF + r], fRS = F[r * ldF + s];
     const int fSR = F[s * ldF + r], fSS = F[s * ldF + s];
     const int qRR = Q[r * ldP + r], qRS = Q[r * ldP + s];
     const int qSR = Q[s * ldP + r], qSS = Q[s * ldP + s];
-    // column-exchange coefficients: (F[x][r]-F[x][s]), (F[r][x]-F[s][x]),
-    // (Q[xb][s]-Q[xb][r]), (Q[s][xb]-Q[r][xb])
-    const int fx_rs = xi ? fSR - fSS : fRR - fRS;
-    const int frs_x = xi ? fRS - fSS : fRR - fSR;
-    const int qxb_sr = xi ? qRS - qRR : qSS - qSR;
-    const int qsr_xb = xi ? qSR - qRR : qSS - qRS;
-    if (gtask) {
-      const int c1 = fx_rs * qxb_sr, c2 = frs_x * qsr_xb;
-      gn[x] = sym ? (DT)2 * ((DT)A + (DT)c1) : (DT)A + (DT)c1 + (DT)c2;
+    if (gt) {
+      // g'[x] = A + (F[x][r]-F[x][s])(Q[xb][s]-Q[xb][r])
+      //           + (F[r][x]-F[s][x])(Q[s][xb]-Q[r][xb])
+      const bool xs = (k == s);
+      if (lg != ((G > 1 && xs) ? 1 : 0)) continue;  // the lane holding Ar or As
+      const int A0 = (G > 1) ? A : (xs ? As : Ar);
+      const int c1 = (xs ? fSR - fSS : fRR - fRS) * (xs ? qRS - qRR : qSS - qSR);
+      const int c2 = (xs ? fRS - fSS : fRR - fSR) * (xs ? qSR - qRR : qSS - qRS);
+      gn[k] = sym ? (DT)2 * ((DT)A0 + (DT)c1) : (DT)A0 + (DT)c1 + (DT)c2;
       continue;
     }
     const int Frk = F[r * ldF + k], Fsk = F[s * ldF + k];
@@ -355,24 +403,39 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
     const int Fkk = F[k * ldF + k], Qkk = Q[k * ldP + k];
     const int a = Frk - Fsk, b = Qrk - Qsk, c = Fkr - Fks, e = Qkr - Qks;
     const DT gk = gc[k] - (DT)(a * b) - (DT)(c * e);
-    const int fxx = xi ? fSS : fRR;  // F[x][x]
-    const int pxx = xi ? qRR : qSS;  // P'[x][x] = Q[xb][xb]
-    const int fxk = xi ? Fsk : Frk;  // F[x][k]
-    const int fkx = xi ? Fks : Fkr;  // F[k][x]
-    const int pxk = xi ? Qrk : Qsk;  // P'[x][k] = Q[xb][k]
-    const int pkx = xi ? Qkr : Qks;  // P'[k][x] = Q[k][xb]
-    const int corr = (fxx - fxk - fkx + Fkk) * (pxx - pxk - pkx + Qkk);
-    const int sig = -fx_rs * e - frs_x * b + qxb_sr * c + qsr_xb * a;
-    const DT cross = sym ? (DT)2 * ((DT)A + (DT)B) : (DT)A + (DT)B;
-    S.R[xi * n + k] = cross + (DT)sig - gk + (DT)corr;
-    if (xi == 0) {
-      S.vec[k] = make_int4(a, b, c, e);
+    for (int xi = lg; xi < 2; xi += (G == 1 ? 1 : 2)) {
+      const bool xs = xi != 0;
+      const int fxx = xs ? fSS : fRR;   // F[x][x]
+      const int pxx = xs ? qRR : qSS;   // P'[x][x] = Q[xb][xb]
+      const int fxk = xs ? Fsk : Frk;   // F[x][k]
+      const int fkx = xs ? Fks : Fkr;   // F[k][x]
+      const int pxk = xs ? Qrk : Qsk;   // P'[x][k] = Q[xb][k]
+      const int pkx = xs ? Qkr : Qks;   // P'[k][x] = Q[k][xb]
+      // exchanged columns: (F[x][r]-F[x][s]), (F[r][x]-F[s][x]),
+      // (Q[xb][s]-Q[xb][r]), (Q[s][xb]-Q[r][xb])
+      const int fx_rs = xs ? fSR - fSS : fRR - fRS;
+      const int frs_x = xs ? fRS - fSS : fRR - fSR;
+      const int qxb_sr = xs ? qRS - qRR : qSS - qSR;
+      const int qsr_xb = xs ? qSR - qRR : qSS - qRS;
+      const int corr = (fxx - fxk - fkx + Fkk) * (pxx - pxk - pkx + Qkk);
+      const int sig = -fx_rs * e - frs_x * b + qxb_sr * c + qsr_xb * a;
+      const int Ax = (G > 1) ? A : (xs ? As : Ar);
+      const int Bx = (G > 1) ? B : (xs ? Bs : Br);
+      const DT cross = sym ? (DT)2 * ((DT)Ax + (DT)Bx) : (DT)Ax + (DT)Bx;
+      S.R[xi * n + k] = cross + (DT)sig - gk + (DT)corr;
+    }
+    if (lg == 0) {
+      reinterpret_cast<typename VO::V*>(S.vec)[k] = VO::pack(a, b, c, e);
       gn[k] = gk;
     }
   }
 }
 
-// Exchange rows and columns r, s of P (and P^T) and p[r], p[s].
+// Exchange rows and columns r, s of P (and P^T) and p[r], p[s], so that
+// P'[i][j] = P[s(i)][s(j)] with s the transposition (r s).  Column entries of
+// the other rows: one thread per (matrix, row); rows r and s: 4-byte words by
+// the last warp (lanes 0-15 for P, 16-31 for P^T), whose lanes then exchange
+// the entries r and s inside those two rows.
 template <int NT>
 __device__ __forceinline__ void swap_rs(int8_t* P, int8_t* Pt, int32_t* perm, int n, int ldP,
                                         bool symD, int r, int s) {
@@ -382,31 +445,34 @@ __device__ __forceinline__ void swap_rs(int8_t* P, int8_t* Pt, int32_t* perm, in
     perm[r] = perm[s];
     perm[s] = t;
   }
-  for (int j = tid; j < n; j += NT) {
-    if (j != r && j != s) {
-      int8_t* Pr = P + r * ldP;
-      int8_t* Ps = P + s * ldP;
-      int8_t t = Pr[j]; Pr[j] = Ps[j]; Ps[j] = t;
-      int8_t* Pj = P + j * ldP;
-      t = Pj[r]; Pj[r] = Pj[s]; Pj[s] = t;
-      if (!symD) {
-        int8_t* Qr = Pt + r * ldP;
-        int8_t* Qs = Pt + s * ldP;
-        t = Qr[j]; Qr[j] = Qs[j]; Qs[j] = t;
-        int8_t* Qj = Pt + j * ldP;
-        t = Qj[r]; Qj[r] = Qj[s]; Qj[s] = t;
+  const int mats = symD ? 1 : 2;
+  for (int c = tid; c < mats * n; c += NT) {
+    const int j = c < n ? c : c - n;
+    if (j == r || j == s) continue;
+    int8_t* Pj = (c < n ? P : Pt) + j * ldP;
+    const int8_t t = Pj[r];
+    Pj[r] = Pj[s];
+    Pj[s] = t;
+  }
+  if (tid >= NT - 32) {
+    const int lane = tid & 31, m = lane >> 4, l = lane & 15;
+    if (m < mats) {
+      int8_t* M = m ? Pt : P;
+      int32_t* Mr = reinterpret_cast<int32_t*>(M + r * ldP);
+      int32_t* Ms = reinterpret_cast<int32_t*>(M + s * ldP);
+      for (int w = l; w < (n + 3) / 4; w += 16) {
+        const int32_t a = Mr[w];
+        Mr[w] = Ms[w];
+        Ms[w] = a;
       }
-    } else if (j == r) {
-      int8_t* Pr = P + r * ldP;
-      int8_t* Ps = P + s * ldP;
-      const int8_t rr = Pr[r], rs = Pr[s], sr = Ps[r], ss = Ps[s];
-      Pr[r] = ss; Pr[s] = sr; Ps[r] = rs; Ps[s] = rr;
-      if (!symD) {
-        int8_t* Qr = Pt + r * ldP;
-        int8_t* Qs = Pt + s * ldP;
-        const int8_t qrr = Qr[r], qrs = Qr[s], qsr = Qs[r], qss = Qs[s];
-        Qr[r] = qss; Qr[s] = qsr; Qs[r] = qrs; Qs[s] = qrr;
-      }
+    }
+    __syncwarp();
+    if (l == 0 && m < mats) {
+      int8_t* M = m ? Pt : P;
+      int8_t* Rr = M + r * ldP;
+      int8_t* Rs = M + s * ldP;
+      int8_t t = Rr[r]; Rr[r] = Rr[s]; Rr[s] = t;
+      t = Rs[r]; Rs[r] = Rs[s]; Rs[s] = t;
     }
   }
 }
@@ -416,22 +482,31 @@ __device__ __forceinline__ void swap_rs(int8_t* P, int8_t* Pt, int32_t* perm, in
 // ---------------------------------------------------------------------------
 constexpr int min_blocks(int nt) { return nt <= 128 ? 4 : nt <= 256 ? 2 : 1; }
 
+// Pairs are handed out as row segments: row u holds the pairs (u, v), v > u;
+// it is cut into segments of at most MAXPT consecutive v, and thread t owns
+// segment t in row-major order.  The host checks that every segment has a
+// thread.
+__host__ __device__ inline int row_segments(int n, int maxpt) {
+  int nseg = 0;
+  for (int u = 0; u < n - 1; ++u) nseg += (n - 1 - u + maxpt - 1) / maxpt;
+  return nseg;
+}
+
 template <typename DT, typename FE, int NT, int MAXPT>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = a.n, ldF = a.ldF, ldP = a.ldP, tid = threadIdx.x, G = a.group;
-  const int T = n * (n - 1) / 2;
   const bool sym = a.symF && a.symD;
   const bool warp0 = tid < 32;
-  const SmemLayout L =
-      smem_layout(n, ldF, (int)sizeof(FE), ldP, a.symF, a.symD, (int)sizeof(DT));
+  const SmemLayout L = smem_layout(n, ldF, (int)sizeof(FE), ldP, a.symF, a.symD,
+                                   (int)sizeof(DT), NT * MAXPT);
   WalkSmem<DT, FE> S;
   S.F = reinterpret_cast<FE*>(smem + L.offF);
   S.Ft = a.symF ? S.F : reinterpret_cast<FE*>(smem + L.offFt);
   S.P = reinterpret_cast<int8_t*>(smem + L.offP);
   S.Pt = a.symD ? S.P : reinterpret_cast<int8_t*>(smem + L.offPt);
   S.tabu = reinterpret_cast<int32_t*>(smem + L.offTabu);
-  S.vec = reinterpret_cast<int4*>(smem + L.offVec);
+  S.vec = smem + L.offVec;
   S.R = reinterpret_cast<DT*>(smem + L.offR);
   S.g0 = reinterpret_cast<DT*>(smem + L.offG0);
   S.g1 = reinterpret_cast<DT*>(smem + L.offG1);
@@ -441,28 +516,25 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
   S.redK = reinterpret_cast<uint32_t*>(smem + L.offRedK);
   S.sum = reinterpret_cast<int64_t*>(smem + L.offSum);
 
-  // Owned pairs: linear index tid + i*NT in lexicographic (u, v) order; the
-  // 16-bit keys (u << 8 | v) of two slots share one register.
-  static_assert(MAXPT % 2 == 0, "keys are packed in pairs");
-  uint32_t kp[MAXPT / 2];
+  // This thread's row segment: pairs (su, sv + i), i < slen.
+  int su = 0, sv = 1, slen = 0;
   {
-    int u = 0, rowStart = 0;
-#pragma unroll
-    for (int i = 0; i < MAXPT; ++i) {
-      const int q = tid + i * NT;
-      uint32_t k16 = kNoPair;
-      if (q < T) {
-        while (q >= rowStart + (n - 1 - u)) {
-          rowStart += n - 1 - u;
-          ++u;
-        }
-        k16 = ((uint32_t)u << 8) | (uint32_t)(u + 1 + (q - rowStart));
+    int t0 = 0;
+    for (int u = 0; u < n - 1; ++u) {
+      const int len = n - 1 - u;
+      const int ns = (len + MAXPT - 1) / MAXPT;
+      if (tid >= t0 && tid < t0 + ns) {
+        const int j = tid - t0;
+        su = u;
+        sv = u + 1 + j * MAXPT;
+        slen = min(MAXPT, len - j * MAXPT);
       }
-      if (i & 1) kp[i / 2] |= k16 << 16;
-      else kp[i / 2] = k16;
+      t0 += ns;
     }
   }
-#define QAP_KEY(i) ((kp[(i) / 2] >> (16 * ((i) & 1))) & 0xffffu)
+  // slots past the longest segment of the warp are skipped by the whole warp
+  const int wlen = __reduce_max_sync(kFull, slen);
+  const uint32_t ukey = (uint32_t)su << 8;
 
   // F (and F^T) once per CTA (rows are whole 16-byte vectors, zero padded);
   // P (and P^T) zeroed once so their padding columns stay zero.
@@ -529,12 +601,9 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
     DT dl[MAXPT];
 #pragma unroll
     for (int i = 0; i < MAXPT; ++i) {
-      dl[i] = 0;
-      if (QAP_KEY(i) != kNoPair) {
-        dl[i] = delta_serial<DT, FE>(S, n, ldF, ldP, sym, (int)(QAP_KEY(i) >> 8),
-                                     (int)(QAP_KEY(i) & 0xffu));
-        S.tabu[tid + i * NT] = 0;
-      }
+      dl[i] = DeltaMax<DT>::v;
+      if (i < slen) dl[i] = delta_serial<DT, FE>(S, n, ldF, ldP, sym, su, sv + i);
+      S.tabu[i * NT + tid] = 0;
     }
 
     DT cur = (DT)c0;
@@ -545,38 +614,47 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
 
     // Owners' pass after move (r, s): new deltas, then the scan for the next
     // iteration `nit` (tabu phase) or the next descent step.  Branch-free per
-    // slot so the shared-memory loads of all slots are in flight together;
-    // slot indexes are clamped in range where a slot holds no pair.
-    auto update_and_scan = [&](uint32_t rs, int r, int s, bool tabu, int nit, int stamp,
-                               DT ncur, DT nbest, DT& bd, uint32_t& bk) {
+    // slot so the shared-memory loads of all slots are in flight together.
+    auto update_and_scan = [&](int r, int s, bool tabu, int nit, int stamp, DT ncur, DT nbest,
+                               DT& bd, uint32_t& bk) {
+      using VO = VecOps<FE>;
+      const auto* vec = reinterpret_cast<const typename VO::V*>(S.vec);
       const DT gr = gn[r], gs = gn[s];
+      const bool tu = (su == r) | (su == s);        // every pair of the segment touches
+      const int ubase = su == r ? 0 : n;
+      const DT gu = su == r ? gr : gs;
+      int ua, ub, uc, ue;
+      VO::unpack(vec[su], ua, ub, uc, ue);
       bd = DeltaMax<DT>::v;
       bk = kNoMove;
 #pragma unroll
       for (int i = 0; i < MAXPT; ++i) {
-        if (i * NT + (tid & ~31) >= T) break;  // whole warp past the last pair
-        const uint32_t k16 = QAP_KEY(i);
-        const bool valid = k16 != kNoPair;
-        const int u = valid ? (int)(k16 >> 8) : 0;
-        const int v = valid ? (int)(k16 & 0xffu) : 0;
-        const int q = valid ? tid + i * NT : 0;
-        const int4 A = S.vec[u], B = S.vec[v];
-        const bool tr = (u == r) | (v == r);
-        const bool ts = (u == s) | (v == s);
-        const int oth = (tr | ts) ? (u ^ v ^ (tr ? r : s)) : 0;
-        const DT rv = S.R[(tr ? 0 : n) + oth];
+        if (i >= wlen) break;
+        const bool valid = i < slen;
+        const int v = valid ? sv + i : sv;
+        int va, vb, vc, ve;
+        VO::unpack(vec[v], va, vb, vc, ve);
+        const bool tvr = v == r, tv = tvr | (v == s);
+        const int idx = tu ? ubase + v : (tvr ? 0 : n) + su;  // in range for any v, su
+        const DT rv = S.R[idx];
+        const int tbl = S.tabu[i * NT + tid];
+        const DT gx = tu ? gu : (tvr ? gr : gs);
         DT d = dl[i];
-        const DT o1 = d + (DT)((A.x - B.x) * (A.y - B.y) + (A.z - B.z) * (A.w - B.w));
-        d = (k16 == rs) ? -d : (tr | ts) ? rv - (tr ? gr : gs) : o1;
-        if (valid) dl[i] = d;
-        if (tabu && k16 == rs) S.tabu[q] = stamp;
-        const bool adm =
-            !tabu || S.tabu[q] <= nit || (a.aspiration && ncur + d < nbest);
+        const DT o1 = d + (DT)((ua - va) * (ub - vb) + (uc - vc) * (ue - ve));
+        const bool isrs = (su == r) & (v == s);
+        d = isrs ? -d : (tu | tv) ? rv - gx : o1;
+        d = valid ? d : DeltaMax<DT>::v;
+        dl[i] = d;
+        // the pair just applied carries its new stamp; the store follows the
+        // loop so no shared-memory store sits between the slots' loads
+        const int tb = isrs ? stamp : tbl;
+        const bool adm = !tabu || tb <= nit || (a.aspiration && ncur + d < nbest);
         if (valid && adm && d < bd) {
           bd = d;
-          bk = k16;
+          bk = ukey | (uint32_t)v;
         }
       }
+      if (tabu && su == r && s >= sv && s < sv + slen) S.tabu[(s - sv) * NT + tid] = stamp;
     };
 
     // ---- 2opt descent (Section 4.1): best move while it improves.
@@ -588,9 +666,9 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
       uint32_t bk = kNoMove;
 #pragma unroll
       for (int i = 0; i < MAXPT; ++i)
-        if (QAP_KEY(i) != kNoPair && dl[i] < bd) {
+        if (i < slen && dl[i] < bd) {
           bd = dl[i];
-          bk = QAP_KEY(i);
+          bk = ukey | (uint32_t)(sv + i);
         }
       for (;;) {
         if (dmoves >= cap) break;
@@ -602,7 +680,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
         if (warp0) dh = fnv_step(dh, r, s);
         phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
         __syncthreads();
-        update_and_scan(bk, r, s, false, 0, 0, cur, cur, bd, bk);
+        update_and_scan(r, s, false, 0, 0, cur, cur, bd, bk);
         swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, a.symD, r, s);
         DT* t = gc; gc = gn; gn = t;
       }
@@ -621,12 +699,11 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
     if (a.iters > 0) {
 #pragma unroll
       for (int i = 0; i < MAXPT; ++i) {
-        if (QAP_KEY(i) == kNoPair) continue;
         const DT d = dl[i];
-        const bool adm = S.tabu[tid + i * NT] <= 1 || (a.aspiration && cur + d < best);
-        if (adm && d < bd) {
+        const bool adm = S.tabu[i * NT + tid] <= 1 || (a.aspiration && cur + d < best);
+        if (i < slen && adm && d < bd) {
           bd = d;
-          bk = QAP_KEY(i);
+          bk = ukey | (uint32_t)(sv + i);
         }
       }
     }
@@ -657,18 +734,12 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
       phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
       __syncthreads();
       int stamp = it + tenure;
-      if (a.period == 0) {
+      if (a.period == 0 && su == r && s >= sv && s < sv + slen) {
         // the paper's rule: a fresh tenure per move, drawn by the owner only
-        bool owner = false;
-#pragma unroll
-        for (int i = 0; i < MAXPT; ++i) owner |= (QAP_KEY(i) == bk);
-        if (owner) {
-          const uint32_t x = walk_draw(a.seed, wid, 1u, (uint32_t)(it - 1));
-          stamp = it + a.tmin + (int)below(x, (uint32_t)(a.tmax - a.tmin + 1));
-        }
+        const uint32_t x = walk_draw(a.seed, wid, 1u, (uint32_t)(it - 1));
+        stamp = it + a.tmin + (int)below(x, (uint32_t)(a.tmax - a.tmin + 1));
       }
-      const uint32_t rs = bk;
-      update_and_scan(rs, r, s, true, it + 1, stamp, cur, best, bd, bk);
+      update_and_scan(r, s, true, it + 1, stamp, cur, best, bd, bk);
       swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, a.symD, r, s);
       DT* t = gc; gc = gn; gn = t;
     }
@@ -692,7 +763,6 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
     }
     __syncthreads();
   }
-#undef QAP_KEY
 }
 
 using WalkKernelFn = void (*)(const WalkArgs);

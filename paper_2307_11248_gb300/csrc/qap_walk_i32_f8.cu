@@ -18,6 +18,7 @@ WalkKernelFn walk_kernel_i32_f8(int nt, int maxpt) {
     case 102408: return walk_kernel<DT, FE, 1024, 8>;
     case 102412: return walk_kernel<DT, FE, 1024, 12>;
     case 102416: return walk_kernel<DT, FE, 1024, 16>;
+    case 102420: return walk_kernel<DT, FE, 1024, 20>;
     default: return nullptr;
   }
 }
