@@ -136,6 +136,11 @@ typedef struct {
   uint64_t seed;           /* Philox key                                     */
   int32_t launch;          /* QAP_LAUNCH_PERSISTENT or QAP_LAUNCH_PLAIN      */
   int32_t threads_per_walk;/* 0 = automatic; else 128, 256, 512 or 1024      */
+  int32_t tenure_per_n;    /* 1: tenure.tmin, tmax, period are tenths of each
+                              instance's n: tmin' = max(1, floor(tmin n / 10)),
+                              tmax' = max(tmin', ceil(tmax n / 10)),
+                              period' = period n / 10 (integer division);
+                              0: absolute                                    */
 } qap_search_params;
 
 /* Per-walk outputs; every pointer may be NULL except best_cost.  For
@@ -207,6 +212,51 @@ qap_status qap_2opt(qap_ctx* ctx, int32_t starts, uint64_t seed, int32_t max_ite
 qap_status qap_tabu(qap_ctx* ctx, int32_t starts, int32_t iters, qap_tenure tenure,
                     int32_t aspiration, uint64_t seed, int32_t* best_p, int64_t* best_cost,
                     int32_t* best_iter, int32_t* status);
+
+/* ------------------------------------------------------------------------
+ * Many instances of uneven n in one persistent launch (the walks of every
+ * instance are independent searches, Sections 4.2 and 4.4).  CTAs take
+ * (instance, walk) items from a device counter, largest n first, and reload
+ * the instance into shared memory when it changes.  Walk k of every instance
+ * uses walk id walk_base + k, so each instance's results equal a qap_search
+ * of that instance alone.
+ * ------------------------------------------------------------------------ */
+typedef struct qap_batch qap_batch;  /* opaque: device copies of all instances */
+
+/* Create a batch.
+ *   count  number of instances, >= 1.
+ *   F, D   host arrays of `count` host pointers; instance i is n[i] x n[i]
+ *          int64, row-major, ranges as for qap_create.  Copied.
+ *   n      host array of `count` sizes, 2 <= n[i] <= 181.
+ *   flags  0 or QAP_FORCE_INT64.  One delta width serves the whole batch:
+ *          int64 if any instance needs it.
+ * Errors: as qap_create, for the first instance that fails. */
+qap_status qap_batch_create(int32_t count, const int64_t* const* F, const int64_t* const* D,
+                            const int32_t* n, uint32_t flags, qap_batch** out);
+void qap_batch_destroy(qap_batch* b);
+
+/* Instance count, largest n and delta width (4 or 8) of a batch; any output
+ * pointer may be NULL. */
+qap_status qap_batch_info(const qap_batch* b, int32_t* count, int32_t* nmax,
+                          int32_t* delta_bytes);
+
+/* Launch shape of a batch search (one plan for the largest n). */
+qap_status qap_batch_plan(qap_batch* b, const qap_search_params* params, qap_plan_info* out);
+
+/* Run params->starts walks of every instance.  Output row i * starts + k
+ * holds walk k of instance i; best_p rows hold p_stride >= max n elements
+ * (the first n[i] are the permutation).  params->launch must be
+ * QAP_LAUNCH_PERSISTENT.
+ * qap_batch_search: host outputs, blocking.
+ * qap_batch_search_async: device outputs, stream-ordered (a counter reset
+ *   and one kernel launch).  The first call for a given (starts, thread
+ *   count) writes device tables synchronously and must not be captured in
+ *   a CUDA graph; later calls can be.
+ * Errors: QAP_EINVAL, QAP_EUNSUPPORTED, QAP_ENOMEM, QAP_ECUDA. */
+qap_status qap_batch_search(qap_batch* b, const qap_search_params* params,
+                            const qap_walk_outputs* out, int32_t p_stride);
+qap_status qap_batch_search_async(qap_batch* b, const qap_search_params* params,
+                                  const qap_walk_outputs* out, int32_t p_stride, void* stream);
 
 #ifdef __cplusplus
 }

@@ -46,7 +46,7 @@ class SearchParams(ctypes.Structure):
                 ("descend", ctypes.c_int32), ("max_descent", ctypes.c_int32),
                 ("iters", ctypes.c_int32), ("tenure", Tenure), ("aspiration", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("launch", ctypes.c_int32),
-                ("threads_per_walk", ctypes.c_int32)]
+                ("threads_per_walk", ctypes.c_int32), ("tenure_per_n", ctypes.c_int32)]
 
 
 class WalkOutputs(ctypes.Structure):
@@ -102,6 +102,21 @@ def lib():
             L.qap_2opt.restype = st
             L.qap_tabu.argtypes = [vp, i32, i32, Tenure, i32, u64, vp, vp, vp, vp]
             L.qap_tabu.restype = st
+            L.qap_batch_create.argtypes = [i32, vp, vp, vp, u32, ctypes.POINTER(vp)]
+            L.qap_batch_create.restype = st
+            L.qap_batch_destroy.argtypes = [vp]
+            L.qap_batch_destroy.restype = None
+            L.qap_batch_info.argtypes = [vp, vp, vp, vp]
+            L.qap_batch_info.restype = st
+            L.qap_batch_plan.argtypes = [vp, ctypes.POINTER(SearchParams),
+                                         ctypes.POINTER(PlanInfo)]
+            L.qap_batch_plan.restype = st
+            L.qap_batch_search.argtypes = [vp, ctypes.POINTER(SearchParams),
+                                           ctypes.POINTER(WalkOutputs), i32]
+            L.qap_batch_search.restype = st
+            L.qap_batch_search_async.argtypes = [vp, ctypes.POINTER(SearchParams),
+                                                 ctypes.POINTER(WalkOutputs), i32, vp]
+            L.qap_batch_search_async.restype = st
             _lib = L
     return _lib
 
@@ -124,10 +139,14 @@ def _ptr(a):
 
 
 def make_params(starts, *, seed=0, iters=0, tenure=(1, 1, 0), aspiration=True, descend=False,
-                max_descent=-1, walk_base=0, launch=LAUNCH_PERSISTENT, threads_per_walk=0):
+                max_descent=-1, walk_base=0, launch=LAUNCH_PERSISTENT, threads_per_walk=0,
+                tenure_per_n=False):
+    """Search parameters.  With tenure_per_n, `tenure` is given in tenths of
+    each instance's n (e.g. (9, 11, 20) is [0.9n, 1.1n] redrawn every 2n)."""
     return SearchParams(int(starts), int(walk_base), int(bool(descend)), int(max_descent),
                         int(iters), Tenure(*[int(t) for t in tenure]), int(bool(aspiration)),
-                        int(seed) & (2**64 - 1), int(launch), int(threads_per_walk))
+                        int(seed) & (2**64 - 1), int(launch), int(threads_per_walk),
+                        int(bool(tenure_per_n)))
 
 
 # ---------------------------------------------------------------------------
@@ -275,3 +294,102 @@ class Instance:
         d_out = {k: v.data_ptr() for k, v in outs.items()}
         qap_search_async(self.h, params, starts.data_ptr() if starts is not None else 0, d_out,
                          stream.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# batches of instances
+# ---------------------------------------------------------------------------
+
+def qap_batch_create(Fs, Ds, flags=0):
+    Fs = [np.ascontiguousarray(F, dtype=np.int64) for F in Fs]
+    Ds = [np.ascontiguousarray(D, dtype=np.int64) for D in Ds]
+    count = len(Fs)
+    ns = np.array([F.shape[0] for F in Fs], dtype=np.int32)
+    fptrs = (ctypes.c_void_p * count)(*[F.ctypes.data for F in Fs])
+    dptrs = (ctypes.c_void_p * count)(*[D.ctypes.data for D in Ds])
+    h = ctypes.c_void_p()
+    _check(lib().qap_batch_create(count, fptrs, dptrs, _ptr(ns), flags, ctypes.byref(h)),
+           "qap_batch_create")
+    return h
+
+
+def qap_batch_destroy(h):
+    lib().qap_batch_destroy(h)
+
+
+def qap_batch_info(h):
+    c, m, d = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().qap_batch_info(h, ctypes.byref(c), ctypes.byref(m), ctypes.byref(d)),
+           "qap_batch_info")
+    return {"count": c.value, "nmax": m.value, "delta_bytes": d.value}
+
+
+def qap_batch_plan(h, params):
+    info = PlanInfo()
+    _check(lib().qap_batch_plan(h, ctypes.byref(params), ctypes.byref(info)), "qap_batch_plan")
+    return {k: getattr(info, k) for k, _ in PlanInfo._fields_}
+
+
+def qap_batch_search(h, params, p_stride):
+    """Blocking batch search; rows i * starts + k; best_p rows of p_stride."""
+    W = qap_batch_info(h)["count"] * params.starts
+    out = {k: np.zeros((W, p_stride) if per_n else W, dtype=dt)
+           for k, (dt, per_n) in OUTPUT_FIELDS.items()}
+    o = WalkOutputs(**{k: out[k].ctypes.data for k in OUTPUT_FIELDS})
+    _check(lib().qap_batch_search(h, ctypes.byref(params), ctypes.byref(o), p_stride),
+           "qap_batch_search")
+    return out
+
+
+def qap_batch_search_async(h, params, d_out, p_stride, stream):
+    o = WalkOutputs(**{k: int(d_out.get(k, 0) or 0) for k in OUTPUT_FIELDS})
+    _check(lib().qap_batch_search_async(h, ctypes.byref(params), ctypes.byref(o), p_stride,
+                                        ctypes.c_void_p(int(stream or 0))),
+           "qap_batch_search_async")
+
+
+class Batch:
+    """Owns one qap_batch (many instances searched in one launch)."""
+
+    def __init__(self, Fs, Ds, force_int64=False):
+        self.ns = [int(np.asarray(F).shape[0]) for F in Fs]
+        self.h = qap_batch_create(Fs, Ds, FORCE_INT64 if force_int64 else 0)
+        self.info = qap_batch_info(self.h)
+        self.p_stride = self.info["nmax"]
+
+    def close(self):
+        if self.h is not None:
+            qap_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def plan(self, params):
+        return qap_batch_plan(self.h, params)
+
+    def search(self, params):
+        return qap_batch_search(self.h, params, self.p_stride)
+
+    def device_outputs(self, walks, device="cuda"):
+        import torch
+        W = self.info["count"] * walks
+        tdt = {np.int32: torch.int32, np.int64: torch.int64, np.uint64: torch.int64}
+        return {k: torch.zeros((W, self.p_stride) if per_n else W, dtype=tdt[dt], device=device)
+                for k, (dt, per_n) in OUTPUT_FIELDS.items()}
+
+    def search_async(self, params, outs, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        qap_batch_search_async(self.h, params, {k: v.data_ptr() for k, v in outs.items()},
+                               self.p_stride, stream.cuda_stream)

@@ -1,5 +1,6 @@
 // C-ABI of the QAP search library: instance upload, validation, launch
-// planning and the blocking / stream-ordered search entry points.
+// planning, and the blocking / stream-ordered search entry points for one
+// instance and for a batch of instances.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -10,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "../../include/qap.h"
@@ -19,6 +21,9 @@ namespace qapk {
 WalkKernelFn walk_kernel_i32_f8(int nt, int maxpt);
 WalkKernelFn walk_kernel_i32_f16(int nt, int maxpt);
 WalkKernelFn walk_kernel_i64_f16(int nt, int maxpt);
+BatchKernelFn batch_kernel_i32_f8(int nt, int maxpt);
+BatchKernelFn batch_kernel_i32_f16(int nt, int maxpt);
+BatchKernelFn batch_kernel_i64_f16(int nt, int maxpt);
 }  // namespace qapk
 
 namespace {
@@ -36,40 +41,20 @@ qap_status cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
   } while (0)
 
-int round_up(int x, int m) { return (x + m - 1) / m * m; }
+#define QAP_TRY(call)                  \
+  do {                                 \
+    qap_status s_ = (call);            \
+    if (s_ != QAP_OK) return s_;       \
+  } while (0)
 
-// Largest n: keys pack (r << 8 | s), and the largest register plan holds
-// 16 pairs per thread for 1024 threads.
+// Largest n: keys pack (r << 8 | s) and the largest register plan holds the
+// row segments of n = 181 with 1024 threads.
 constexpr int kMaxN = 181;
 
 struct Plan {
   int nt;
   int maxpt;
 };
-
-}  // namespace
-
-struct qap_ctx {
-  int device = 0;
-  int n = 0, ldF = 0, ldP = 0;
-  int symF = 0, symD = 0;
-  int dbytes = 4;  // delta width
-  int fbytes = 2;  // flow element width in device memory (1: int8, 2: int16)
-  int64_t bound = 0;
-  int sms = 0;
-  int smem_optin = 0;
-  void* dF = nullptr;
-  void* dFt = nullptr;
-  int8_t* dD = nullptr;
-  cudaStream_t stream = nullptr;
-  // growable device buffers for the blocking entry points
-  void* scratch = nullptr;
-  size_t scratch_bytes = 0;
-};
-
-namespace {
-
-using KernelFn = qapk::WalkKernelFn;
 
 // Register plans (threads per walk, pair slots per thread) compiled into the
 // library.  A plan fits n when its row segments (qapk::row_segments) number
@@ -102,33 +87,104 @@ bool choose_plan(int n, int threads, Plan* out) {
   return false;
 }
 
-KernelFn pick_kernel(const qap_ctx* ctx, const Plan& p) {
-  if (ctx->dbytes == 8) return qapk::walk_kernel_i64_f16(p.nt, p.maxpt);
-  if (ctx->fbytes == 1) return qapk::walk_kernel_i32_f8(p.nt, p.maxpt);
+// Widest power-of-two group (<= 8 lanes, <= the row chunks) that still gives
+// every index of phase X its own group.
+int group_for(int n, int nt, int fbytes) {
+  const int w = 16 / fbytes;
+  const int nc = (n + w - 1) / w;
+  int g = 8;
+  while (g > 1 && (nt / g < n || g > nc)) g >>= 1;
+  return g;
+}
+
+// One instance's shape on the device: F, F^T in `fbytes` elements with rows
+// of an odd number of 16-byte chunks (rows read side by side by the lanes of
+// a warp then fall in different banks), D as int8.
+struct DevInstance {
+  int n = 0, ldF = 0, ldP = 0, symF = 0, symD = 0;
+  int64_t bound = 0;
+  int64_t maxF = 0;
+};
+
+int pad_ldF(int n, int fbytes) { return (16 / fbytes) * (((n * fbytes + 15) / 16) | 1); }
+int pad_ldP(int n) { return 16 * (((n + 15) / 16) | 1); }
+
+// Checks ranges and symmetry of one instance.
+qap_status inspect_instance(const int64_t* F, const int64_t* D, int n, DevInstance* di) {
+  if (!F || !D || n < 2) return QAP_EINVAL;
+  if (n > kMaxN) return QAP_EUNSUPPORTED;
+  int64_t mF = 0, mD = 0;
+  int symF = 1, symD = 1;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const int64_t f = F[(size_t)i * n + j], d = D[(size_t)i * n + j];
+      if (f < INT16_MIN || f > INT16_MAX || d < INT8_MIN || d > INT8_MAX) return QAP_EUNSUPPORTED;
+      mF = std::max<int64_t>(mF, f < 0 ? -f : f);
+      mD = std::max<int64_t>(mD, d < 0 ? -d : d);
+      if (f != F[(size_t)j * n + i]) symF = 0;
+      if (d != D[(size_t)j * n + i]) symD = 0;
+    }
+  const int64_t nn = n;
+  di->n = n;
+  di->symF = symF;
+  di->symD = symD;
+  di->bound = (nn * nn + 8 * nn + 32) * mF * mD;  // < 2^40 for n <= 181
+  di->maxF = mF;
+  return QAP_OK;
+}
+
+// Host images of F, F^T and D for the chosen element width.
+void build_images(const int64_t* F, const int64_t* D, const DevInstance& di, int fbytes,
+                  std::vector<unsigned char>& img_F, std::vector<unsigned char>& img_Ft,
+                  std::vector<unsigned char>& img_D) {
+  const int n = di.n, ld = di.ldF;
+  img_F.assign((size_t)n * ld * fbytes, 0);
+  img_Ft.assign((size_t)n * ld * fbytes, 0);
+  img_D.resize((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const int64_t f = F[(size_t)i * n + j];
+      if (fbytes == 1) {
+        reinterpret_cast<int8_t*>(img_F.data())[(size_t)i * ld + j] = (int8_t)f;
+        reinterpret_cast<int8_t*>(img_Ft.data())[(size_t)j * ld + i] = (int8_t)f;
+      } else {
+        reinterpret_cast<int16_t*>(img_F.data())[(size_t)i * ld + j] = (int16_t)f;
+        reinterpret_cast<int16_t*>(img_Ft.data())[(size_t)j * ld + i] = (int16_t)f;
+      }
+      img_D[(size_t)i * n + j] = (unsigned char)(int8_t)D[(size_t)i * n + j];
+    }
+}
+
+qap_status device_attrs(int* device, int* sms, int* smem_optin) {
+  QAP_CUDA(cudaGetDevice(device));
+  QAP_CUDA(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, *device));
+  QAP_CUDA(cudaDeviceGetAttribute(smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, *device));
+  return QAP_OK;
+}
+
+qapk::WalkKernelFn pick_walk_kernel(int dbytes, int fbytes, const Plan& p) {
+  if (dbytes == 8) return qapk::walk_kernel_i64_f16(p.nt, p.maxpt);
+  if (fbytes == 1) return qapk::walk_kernel_i32_f8(p.nt, p.maxpt);
   return qapk::walk_kernel_i32_f16(p.nt, p.maxpt);
+}
+
+qapk::BatchKernelFn pick_batch_kernel(int dbytes, int fbytes, const Plan& p) {
+  if (dbytes == 8) return qapk::batch_kernel_i64_f16(p.nt, p.maxpt);
+  if (fbytes == 1) return qapk::batch_kernel_i32_f8(p.nt, p.maxpt);
+  return qapk::batch_kernel_i32_f16(p.nt, p.maxpt);
 }
 
 std::mutex g_attr_mu;
 
-qap_status prepare_kernel(KernelFn fn, int smem) {
+qap_status prepare_kernel(const void* fn, int smem) {
   // cudaFuncSetAttribute is idempotent; serialise to keep it cheap and safe.
   std::lock_guard<std::mutex> lk(g_attr_mu);
-  QAP_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  QAP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   return QAP_OK;
 }
 
-struct Launch {
-  KernelFn fn;
-  Plan plan;
-  int group;  // lanes per recompute task
-  int smem;
-  int ctas_per_sm;
-  int grid;
-};
-
-qap_status validate_params(const qap_ctx* ctx, const qap_search_params* p) {
-  if (!ctx || !p) return QAP_EINVAL;
+qap_status validate_params(const qap_search_params* p) {
+  if (!p) return QAP_EINVAL;
   if (p->starts < 1 || p->iters < 0) return QAP_EINVAL;
   if (p->descend != 0 && p->descend != 1) return QAP_EINVAL;
   if (p->aspiration != 0 && p->aspiration != 1) return QAP_EINVAL;
@@ -139,52 +195,21 @@ qap_status validate_params(const qap_ctx* ctx, const qap_search_params* p) {
     if ((int64_t)p->iters + (int64_t)p->tenure.tmax >= (int64_t)INT_MAX) return QAP_EINVAL;
   }
   if (p->launch != QAP_LAUNCH_PERSISTENT && p->launch != QAP_LAUNCH_PLAIN) return QAP_EINVAL;
+  if (p->tenure_per_n != 0 && p->tenure_per_n != 1) return QAP_EINVAL;
+  if (p->tenure_per_n && p->iters > 0 &&
+      ((int64_t)p->tenure.tmax * kMaxN / 10 + 1 + p->iters >= (int64_t)INT_MAX ||
+       (int64_t)p->tenure.period * kMaxN > (int64_t)INT_MAX))
+    return QAP_EINVAL;
   const int t = p->threads_per_walk;
   if (t != 0 && t != 128 && t != 256 && t != 512 && t != 1024) return QAP_EINVAL;
   return QAP_OK;
 }
 
-qap_status plan_launch(qap_ctx* ctx, const qap_search_params* p, Launch* L) {
-  if (!choose_plan(ctx->n, p->threads_per_walk, &L->plan)) return QAP_EUNSUPPORTED;
-  L->fn = pick_kernel(ctx, L->plan);
-  if (!L->fn) return QAP_EUNSUPPORTED;
-  const qapk::SmemLayout S =
-      qapk::smem_layout(ctx->n, ctx->ldF, ctx->fbytes, ctx->ldP, ctx->symF, ctx->symD,
-                        ctx->dbytes, L->plan.nt * L->plan.maxpt);
-  L->smem = S.bytes;
-  if (L->smem > ctx->smem_optin) return QAP_EUNSUPPORTED;
-  qap_status st = prepare_kernel(L->fn, L->smem);
-  if (st != QAP_OK) return st;
-  int occ = 0;
-  QAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &occ, reinterpret_cast<const void*>(L->fn), L->plan.nt, L->smem));
-  if (occ < 1) return QAP_EUNSUPPORTED;
-  L->ctas_per_sm = occ;
-  L->grid = std::min(p->starts, occ * ctx->sms);
-  // widest power-of-two group (<= 8 lanes, <= the row chunks) that still
-  // gives every index of phase X its own group
-  const int nc = (ctx->n + 16 / ctx->fbytes - 1) / (16 / ctx->fbytes);
-  L->group = 8;
-  while (L->group > 1 && (L->plan.nt / L->group < ctx->n || L->group > nc)) L->group >>= 1;
-  return QAP_OK;
-}
-
-qapk::WalkArgs make_args(const qap_ctx* ctx, const qap_search_params* p, const int32_t* d_starts,
-                         const qap_walk_outputs* o) {
-  qapk::WalkArgs a{};
-  a.n = ctx->n;
-  a.ldF = ctx->ldF;
-  a.ldP = ctx->ldP;
-  a.symF = ctx->symF;
-  a.symD = ctx->symD;
-  a.F = ctx->dF;
-  a.Ft = ctx->symF ? ctx->dF : ctx->dFt;
-  a.D = ctx->dD;
-  a.walks = p->starts;
-  a.walk_offset = 0;
+qapk::SearchArgs make_search_args(const qap_search_params* p, const qap_walk_outputs* o,
+                                  int p_stride) {
+  qapk::SearchArgs a{};
   a.walk_base = p->walk_base;
   a.seed = p->seed;
-  a.starts = d_starts;
   a.descend = p->descend;
   a.max_descent = p->max_descent;
   a.iters = p->iters;
@@ -192,6 +217,8 @@ qapk::WalkArgs make_args(const qap_ctx* ctx, const qap_search_params* p, const i
   a.tmax = p->tenure.tmax;
   a.period = p->tenure.period;
   a.aspiration = p->aspiration;
+  a.tenure_per_n = p->tenure_per_n;
+  a.p_stride = p_stride;
   a.best_p = o->best_p;
   a.best_cost = o->best_cost;
   a.final_cost = o->final_cost;
@@ -213,17 +240,203 @@ bool is_permutation(const int32_t* p, int n, std::vector<char>& seen) {
   return true;
 }
 
-qap_status ensure_scratch(qap_ctx* ctx, size_t bytes) {
-  if (bytes <= ctx->scratch_bytes) return QAP_OK;
-  if (ctx->scratch) {
-    cudaFree(ctx->scratch);
-    ctx->scratch = nullptr;
-    ctx->scratch_bytes = 0;
+qap_status grow(void** buf, size_t* have, size_t bytes) {
+  if (bytes <= *have) return QAP_OK;
+  if (*buf) {
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
   }
-  cudaError_t e = cudaMalloc(&ctx->scratch, bytes);
+  cudaError_t e = cudaMalloc(buf, bytes);
   if (e == cudaErrorMemoryAllocation) return QAP_ENOMEM;
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-  ctx->scratch_bytes = bytes;
+  *have = bytes;
+  return QAP_OK;
+}
+
+// Device outputs of W walks carved from one buffer; rows of best_p hold
+// p_stride elements.
+struct OutLayout {
+  size_t off_p, off_i64, off_i32, total;
+};
+
+OutLayout out_layout(int W, int p_stride) {
+  OutLayout L;
+  const size_t perm = (size_t)W * p_stride * sizeof(int32_t);
+  L.off_p = 0;
+  L.off_i64 = (perm + 255) / 256 * 256;
+  L.off_i32 = L.off_i64 + (size_t)4 * W * 8;
+  L.total = L.off_i32 + (size_t)4 * W * 4 + 256;
+  return L;
+}
+
+qap_walk_outputs carve_outputs(char* base, const OutLayout& L, int W) {
+  qap_walk_outputs d{};
+  d.best_p = reinterpret_cast<int32_t*>(base + L.off_p);
+  int64_t* i64 = reinterpret_cast<int64_t*>(base + L.off_i64);
+  int32_t* i32 = reinterpret_cast<int32_t*>(base + L.off_i32);
+  d.best_cost = i64;
+  d.final_cost = i64 + W;
+  d.hash = reinterpret_cast<uint64_t*>(i64 + 2 * W);
+  d.descent_hash = reinterpret_cast<uint64_t*>(i64 + 3 * W);
+  d.best_iter = i32;
+  d.iters_done = i32 + W;
+  d.status = i32 + 2 * W;
+  d.descent_moves = i32 + 3 * W;
+  return d;
+}
+
+qap_status copy_outputs_back(const qap_walk_outputs* out, const qap_walk_outputs& d, int W,
+                             int p_stride, cudaStream_t s) {
+  auto d2h = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) : cudaSuccess;
+  };
+  QAP_CUDA(d2h(out->best_p, d.best_p, (size_t)W * p_stride * 4));
+  QAP_CUDA(d2h(out->best_cost, d.best_cost, (size_t)W * 8));
+  QAP_CUDA(d2h(out->final_cost, d.final_cost, (size_t)W * 8));
+  QAP_CUDA(d2h(out->hash, d.hash, (size_t)W * 8));
+  QAP_CUDA(d2h(out->descent_hash, d.descent_hash, (size_t)W * 8));
+  QAP_CUDA(d2h(out->best_iter, d.best_iter, (size_t)W * 4));
+  QAP_CUDA(d2h(out->iters_done, d.iters_done, (size_t)W * 4));
+  QAP_CUDA(d2h(out->status, d.status, (size_t)W * 4));
+  QAP_CUDA(d2h(out->descent_moves, d.descent_moves, (size_t)W * 4));
+  QAP_CUDA(cudaStreamSynchronize(s));
+  return QAP_OK;
+}
+
+}  // namespace
+
+struct qap_ctx {
+  int device = 0, sms = 0, smem_optin = 0;
+  DevInstance di;
+  int dbytes = 4;  // delta width
+  int fbytes = 2;  // flow element width in device memory (1: int8, 2: int16)
+  void* dF = nullptr;
+  void* dFt = nullptr;
+  int8_t* dD = nullptr;
+  cudaStream_t stream = nullptr;
+  // growable device buffer of the blocking entry points
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+
+struct qap_batch {
+  int device = 0, sms = 0, smem_optin = 0;
+  int count = 0, nmax = 0;
+  int dbytes = 4, fbytes = 2;
+  std::vector<DevInstance> di;
+  std::vector<size_t> offF, offFt, offD;
+  void* data = nullptr;  // every instance's F, F^T and D
+  qapk::InstArgs* d_insts = nullptr;
+  int cached_nt = 0;     // plan the instance table was written for
+  int32_t* d_items = nullptr;  // item_inst | item_walk | row_base
+  int cached_walks = 0;
+  int* d_counter = nullptr;
+  cudaStream_t stream = nullptr;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+
+namespace {
+
+struct Launch {
+  const void* fn;
+  Plan plan;
+  int smem;
+  int ctas_per_sm;
+  int grid;
+};
+
+qap_status occupancy(Launch* L, int sms, int work) {
+  int occ = 0;
+  QAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L->fn, L->plan.nt, L->smem));
+  if (occ < 1) return QAP_EUNSUPPORTED;
+  L->ctas_per_sm = occ;
+  L->grid = std::min(work, occ * sms);
+  return QAP_OK;
+}
+
+qap_status plan_ctx(qap_ctx* ctx, const qap_search_params* p, Launch* L) {
+  if (!choose_plan(ctx->di.n, p->threads_per_walk, &L->plan)) return QAP_EUNSUPPORTED;
+  L->fn = reinterpret_cast<const void*>(pick_walk_kernel(ctx->dbytes, ctx->fbytes, L->plan));
+  if (!L->fn) return QAP_EUNSUPPORTED;
+  const DevInstance& d = ctx->di;
+  L->smem = qapk::smem_layout(d.n, d.ldF, ctx->fbytes, d.ldP, d.symF, d.symD, ctx->dbytes,
+                              L->plan.nt * L->plan.maxpt)
+                .bytes;
+  if (L->smem > ctx->smem_optin) return QAP_EUNSUPPORTED;
+  QAP_TRY(prepare_kernel(L->fn, L->smem));
+  return occupancy(L, ctx->sms, p->starts);
+}
+
+qapk::InstArgs inst_args(const DevInstance& d, const void* F, const void* Ft, const int8_t* D,
+                         int nt, int fbytes) {
+  qapk::InstArgs I{};
+  I.n = d.n;
+  I.ldF = d.ldF;
+  I.ldP = d.ldP;
+  I.symF = d.symF;
+  I.symD = d.symD;
+  I.group = group_for(d.n, nt, fbytes);
+  I.F = F;
+  I.Ft = d.symF ? F : Ft;
+  I.D = D;
+  return I;
+}
+
+qap_status plan_batch(qap_batch* b, const qap_search_params* p, Launch* L) {
+  if (!choose_plan(b->nmax, p->threads_per_walk, &L->plan)) return QAP_EUNSUPPORTED;
+  L->fn = reinterpret_cast<const void*>(pick_batch_kernel(b->dbytes, b->fbytes, L->plan));
+  if (!L->fn) return QAP_EUNSUPPORTED;
+  int smem = 0;
+  for (const DevInstance& d : b->di)
+    smem = std::max(smem, qapk::smem_layout(d.n, d.ldF, b->fbytes, d.ldP, d.symF, d.symD,
+                                            b->dbytes, L->plan.nt * L->plan.maxpt)
+                              .bytes);
+  L->smem = smem;
+  // the batch kernel also holds one static int
+  if (L->smem + 16 > b->smem_optin) return QAP_EUNSUPPORTED;
+  QAP_TRY(prepare_kernel(L->fn, L->smem));
+  return occupancy(L, b->sms, b->count * p->starts);
+}
+
+// Writes the instance table for thread count nt and the item lists for W
+// walks per instance (longest instances first), synchronously; the results
+// are cached, so later calls with the same nt and W only launch.
+qap_status batch_tables(qap_batch* b, int nt, int W) {
+  if (b->cached_nt != nt) {
+    std::vector<qapk::InstArgs> h(b->count);
+    char* base = static_cast<char*>(b->data);
+    for (int i = 0; i < b->count; ++i)
+      h[i] = inst_args(b->di[i], base + b->offF[i], base + b->offFt[i],
+                       reinterpret_cast<int8_t*>(base + b->offD[i]), nt, b->fbytes);
+    QAP_CUDA(cudaMemcpy(b->d_insts, h.data(), sizeof(qapk::InstArgs) * b->count,
+                        cudaMemcpyHostToDevice));
+    b->cached_nt = nt;
+  }
+  if (b->cached_walks != W) {
+    const size_t items = (size_t)b->count * W;
+    if (items > (size_t)INT_MAX / 2) return QAP_EINVAL;
+    std::vector<int> order(b->count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return b->di[x].n > b->di[y].n; });
+    std::vector<int32_t> h(items * 2 + b->count);
+    size_t k = 0;
+    for (int inst : order)
+      for (int w = 0; w < W; ++w, ++k) {
+        h[k] = inst;
+        h[items + k] = w;
+      }
+    for (int i = 0; i < b->count; ++i) h[2 * items + i] = i * W;
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_items = nullptr;
+    b->cached_walks = 0;
+    if (cudaMalloc(&b->d_items, h.size() * sizeof(int32_t)) != cudaSuccess) return QAP_ENOMEM;
+    QAP_CUDA(cudaMemcpy(b->d_items, h.data(), h.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice));
+    b->cached_walks = W;
+  }
   return QAP_OK;
 }
 
@@ -246,83 +459,40 @@ const char* qap_strerror(qap_status s) {
 
 const char* qap_last_error(void) { return g_last_error; }
 
+// ---------------------------------------------------------------------------
+// one instance
+// ---------------------------------------------------------------------------
+
 qap_status qap_create(const int64_t* F, const int64_t* D, int32_t n, uint32_t flags,
                       qap_ctx** out) {
   if (!out) return QAP_EINVAL;
   *out = nullptr;
-  if (!F || !D || n < 2) return QAP_EINVAL;
   if (flags & ~QAP_FORCE_INT64) return QAP_EINVAL;
-  if (n > kMaxN) return QAP_EUNSUPPORTED;
-  int64_t mF = 0, mD = 0;
-  int symF = 1, symD = 1;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      const int64_t f = F[(size_t)i * n + j], d = D[(size_t)i * n + j];
-      if (f < INT16_MIN || f > INT16_MAX || d < INT8_MIN || d > INT8_MAX) return QAP_EUNSUPPORTED;
-      mF = std::max<int64_t>(mF, f < 0 ? -f : f);
-      mD = std::max<int64_t>(mD, d < 0 ? -d : d);
-      if (f != F[(size_t)j * n + i]) symF = 0;
-      if (d != D[(size_t)j * n + i]) symD = 0;
-    }
-  const int64_t nn = (int64_t)n;
-  const int64_t bound = (nn * nn + 8 * nn + 32) * mF * mD;  // < 2^40 for n <= 181
+  DevInstance di;
+  QAP_TRY(inspect_instance(F, D, n, &di));
   qap_ctx* c = new (std::nothrow) qap_ctx();
   if (!c) return QAP_ENOMEM;
-  c->n = n;
-  c->symF = symF;
-  c->symD = symD;
-  c->bound = bound;
-  c->dbytes = ((flags & QAP_FORCE_INT64) || bound > (int64_t)INT_MAX - 1) ? 8 : 4;
-  // int8 flows (dp4a rows) when they fit and deltas are int32; else int16
-  c->fbytes = (mF <= 127 && c->dbytes == 4) ? 1 : 2;
-  // F rows: an odd number of 16-byte chunks, so rows read side by side by
-  // the lanes of a warp fall in different banks
-  c->ldF = (16 / c->fbytes) * (((n * c->fbytes + 15) / 16) | 1);
-  // P rows: an odd number of 16-byte chunks, so the column exchanges of a
-  // move hit 8 different banks per 32 rows instead of 2
-  c->ldP = 16 * (((n + 15) / 16) | 1);
   auto fail = [&](qap_status s) {
     qap_destroy(c);
     return s;
   };
-  cudaError_t e = cudaGetDevice(&c->device);
-  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaGetDevice"));
-  e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
-  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
-  e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
-  const size_t fcount = (size_t)n * c->ldF;
-  std::vector<int16_t> hF16, hFt16;
-  std::vector<int8_t> hF8, hFt8;
-  if (c->fbytes == 1) {
-    hF8.assign(fcount, 0);
-    hFt8.assign(fcount, 0);
-  } else {
-    hF16.assign(fcount, 0);
-    hFt16.assign(fcount, 0);
-  }
-  std::vector<int8_t> hD((size_t)n * n);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      const int64_t f = F[(size_t)i * n + j];
-      if (c->fbytes == 1) {
-        hF8[(size_t)i * c->ldF + j] = (int8_t)f;
-        hFt8[(size_t)j * c->ldF + i] = (int8_t)f;
-      } else {
-        hF16[(size_t)i * c->ldF + j] = (int16_t)f;
-        hFt16[(size_t)j * c->ldF + i] = (int16_t)f;
-      }
-      hD[(size_t)i * n + j] = (int8_t)D[(size_t)i * n + j];
-    }
-  const void* srcF = c->fbytes == 1 ? (const void*)hF8.data() : (const void*)hF16.data();
-  const void* srcFt = c->fbytes == 1 ? (const void*)hFt8.data() : (const void*)hFt16.data();
-  const size_t fbytes = fcount * c->fbytes;
-  if (cudaMalloc(&c->dF, fbytes) != cudaSuccess) return fail(QAP_ENOMEM);
-  if (!symF && cudaMalloc(&c->dFt, fbytes) != cudaSuccess) return fail(QAP_ENOMEM);
-  if (cudaMalloc(&c->dD, hD.size()) != cudaSuccess) return fail(QAP_ENOMEM);
-  e = cudaMemcpy(c->dF, srcF, fbytes, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !symF) e = cudaMemcpy(c->dFt, srcFt, fbytes, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(c->dD, hD.data(), hD.size(), cudaMemcpyHostToDevice);
+  c->dbytes = ((flags & QAP_FORCE_INT64) || di.bound > (int64_t)INT_MAX - 1) ? 8 : 4;
+  // int8 flows (dp4a rows) when they fit and deltas are int32; else int16
+  c->fbytes = (di.maxF <= 127 && c->dbytes == 4) ? 1 : 2;
+  di.ldF = pad_ldF(n, c->fbytes);
+  di.ldP = pad_ldP(n);
+  c->di = di;
+  qap_status st = device_attrs(&c->device, &c->sms, &c->smem_optin);
+  if (st != QAP_OK) return fail(st);
+  std::vector<unsigned char> iF, iFt, iD;
+  build_images(F, D, di, c->fbytes, iF, iFt, iD);
+  if (cudaMalloc(&c->dF, iF.size()) != cudaSuccess) return fail(QAP_ENOMEM);
+  if (!di.symF && cudaMalloc(&c->dFt, iFt.size()) != cudaSuccess) return fail(QAP_ENOMEM);
+  if (cudaMalloc(&c->dD, iD.size()) != cudaSuccess) return fail(QAP_ENOMEM);
+  cudaError_t e = cudaMemcpy(c->dF, iF.data(), iF.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !di.symF)
+    e = cudaMemcpy(c->dFt, iFt.data(), iFt.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->dD, iD.data(), iD.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
   e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreateWithFlags"));
@@ -343,22 +513,20 @@ void qap_destroy(qap_ctx* ctx) {
 
 qap_status qap_info(const qap_ctx* ctx, qap_ctx_info* out) {
   if (!ctx || !out) return QAP_EINVAL;
-  out->n = ctx->n;
+  out->n = ctx->di.n;
   out->delta_bytes = ctx->dbytes;
-  out->sym_flow = ctx->symF;
-  out->sym_dist = ctx->symD;
-  out->bound = ctx->bound;
+  out->sym_flow = ctx->di.symF;
+  out->sym_dist = ctx->di.symD;
+  out->bound = ctx->di.bound;
   return QAP_OK;
 }
 
 qap_status qap_plan(qap_ctx* ctx, const qap_search_params* params, qap_plan_info* out) {
-  qap_status st = validate_params(ctx, params);
-  if (st != QAP_OK) return st;
-  if (!out) return QAP_EINVAL;
+  if (!ctx || !out) return QAP_EINVAL;
+  QAP_TRY(validate_params(params));
   QAP_CUDA(cudaSetDevice(ctx->device));
   Launch L;
-  st = plan_launch(ctx, params, &L);
-  if (st != QAP_OK) return st;
+  QAP_TRY(plan_ctx(ctx, params, &L));
   out->threads_per_walk = L.plan.nt;
   out->pairs_per_thread = L.plan.maxpt;
   out->smem_bytes = L.smem;
@@ -371,24 +539,28 @@ qap_status qap_plan(qap_ctx* ctx, const qap_search_params* params, qap_plan_info
 qap_status qap_search_async(qap_ctx* ctx, const qap_search_params* params,
                             const int32_t* d_starts, const qap_walk_outputs* out,
                             void* stream) {
-  qap_status st = validate_params(ctx, params);
-  if (st != QAP_OK) return st;
+  if (!ctx) return QAP_EINVAL;
+  QAP_TRY(validate_params(params));
   if (!out || !out->best_cost) return QAP_EINVAL;
   QAP_CUDA(cudaSetDevice(ctx->device));
   Launch L;
-  st = plan_launch(ctx, params, &L);
-  if (st != QAP_OK) return st;
+  QAP_TRY(plan_ctx(ctx, params, &L));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  qapk::WalkArgs a = make_args(ctx, params, d_starts, out);
-  a.group = L.group;
+  qapk::WalkArgs a{};
+  a.inst = inst_args(ctx->di, ctx->dF, ctx->dFt, ctx->dD, L.plan.nt, ctx->fbytes);
+  a.s = make_search_args(params, out, ctx->di.n);
+  a.starts = d_starts;
+  a.walks = params->starts;
+  a.walk_offset = 0;
+  const auto fn = reinterpret_cast<qapk::WalkKernelFn>(const_cast<void*>(L.fn));
   if (params->launch == QAP_LAUNCH_PLAIN) {
     a.walks = 1;
     for (int w = 0; w < params->starts; ++w) {
       a.walk_offset = w;
-      L.fn<<<1, L.plan.nt, L.smem, s>>>(a);
+      fn<<<1, L.plan.nt, L.smem, s>>>(a);
     }
   } else {
-    L.fn<<<L.grid, L.plan.nt, L.smem, s>>>(a);
+    fn<<<L.grid, L.plan.nt, L.smem, s>>>(a);
   }
   QAP_CUDA(cudaGetLastError());
   return QAP_OK;
@@ -396,72 +568,40 @@ qap_status qap_search_async(qap_ctx* ctx, const qap_search_params* params,
 
 qap_status qap_search(qap_ctx* ctx, const qap_search_params* params, const int32_t* starts,
                       const qap_walk_outputs* out) {
-  qap_status st = validate_params(ctx, params);
-  if (st != QAP_OK) return st;
+  if (!ctx) return QAP_EINVAL;
+  QAP_TRY(validate_params(params));
   if (!out || !out->best_cost) return QAP_EINVAL;
-  const int n = ctx->n, W = params->starts;
+  const int n = ctx->di.n, W = params->starts;
   if (starts) {
     std::vector<char> seen;
     for (int w = 0; w < W; ++w)
       if (!is_permutation(starts + (size_t)w * n, n, seen)) return QAP_EINVAL;
   }
   QAP_CUDA(cudaSetDevice(ctx->device));
-  // device layout of the scratch block: starts | best_p | 64-bit outputs | 32-bit outputs
-  const size_t perm_bytes = (size_t)W * n * sizeof(int32_t);
-  const size_t off_best_p = 0;
-  const size_t off_starts = off_best_p + ((perm_bytes + 255) / 256) * 256;
-  const size_t off_i64 = off_starts + ((perm_bytes + 255) / 256) * 256;
-  const size_t n64 = 4, n32 = 5;
-  const size_t off_i32 = off_i64 + n64 * W * 8;
-  const size_t total = off_i32 + n32 * W * 4 + 256;
-  st = ensure_scratch(ctx, total);
-  if (st != QAP_OK) return st;
+  const OutLayout L = out_layout(W, n);
+  const size_t starts_off = (L.total + 255) / 256 * 256;
+  QAP_TRY(grow(&ctx->scratch, &ctx->scratch_bytes, starts_off + (size_t)W * n * 4));
   char* base = static_cast<char*>(ctx->scratch);
-  qap_walk_outputs d{};
-  d.best_p = reinterpret_cast<int32_t*>(base + off_best_p);
-  int32_t* d_starts = reinterpret_cast<int32_t*>(base + off_starts);
-  int64_t* i64 = reinterpret_cast<int64_t*>(base + off_i64);
-  int32_t* i32 = reinterpret_cast<int32_t*>(base + off_i32);
-  d.best_cost = i64;
-  d.final_cost = i64 + W;
-  d.hash = reinterpret_cast<uint64_t*>(i64 + 2 * W);
-  d.descent_hash = reinterpret_cast<uint64_t*>(i64 + 3 * W);
-  d.best_iter = i32;
-  d.iters_done = i32 + W;
-  d.status = i32 + 2 * W;
-  d.descent_moves = i32 + 3 * W;
+  const qap_walk_outputs d = carve_outputs(base, L, W);
+  int32_t* d_starts = reinterpret_cast<int32_t*>(base + starts_off);
   cudaStream_t s = ctx->stream;
-  if (starts) QAP_CUDA(cudaMemcpyAsync(d_starts, starts, perm_bytes, cudaMemcpyHostToDevice, s));
-  st = qap_search_async(ctx, params, starts ? d_starts : nullptr, &d, s);
-  if (st != QAP_OK) return st;
-  auto d2h = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
-    return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) : cudaSuccess;
-  };
-  QAP_CUDA(d2h(out->best_p, d.best_p, perm_bytes));
-  QAP_CUDA(d2h(out->best_cost, d.best_cost, (size_t)W * 8));
-  QAP_CUDA(d2h(out->final_cost, d.final_cost, (size_t)W * 8));
-  QAP_CUDA(d2h(out->hash, d.hash, (size_t)W * 8));
-  QAP_CUDA(d2h(out->descent_hash, d.descent_hash, (size_t)W * 8));
-  QAP_CUDA(d2h(out->best_iter, d.best_iter, (size_t)W * 4));
-  QAP_CUDA(d2h(out->iters_done, d.iters_done, (size_t)W * 4));
-  QAP_CUDA(d2h(out->status, d.status, (size_t)W * 4));
-  QAP_CUDA(d2h(out->descent_moves, d.descent_moves, (size_t)W * 4));
-  QAP_CUDA(cudaStreamSynchronize(s));
-  return QAP_OK;
+  if (starts)
+    QAP_CUDA(cudaMemcpyAsync(d_starts, starts, (size_t)W * n * 4, cudaMemcpyHostToDevice, s));
+  QAP_TRY(qap_search_async(ctx, params, starts ? d_starts : nullptr, &d, s));
+  return copy_outputs_back(out, d, W, n, s);
 }
 
 qap_status qap_cost(qap_ctx* ctx, int32_t count, const int32_t* p, int64_t* cost) {
   if (!ctx || count < 0 || (count > 0 && (!p || !cost))) return QAP_EINVAL;
   if (count == 0) return QAP_OK;
-  const int n = ctx->n;
+  const int n = ctx->di.n;
   std::vector<char> seen;
   for (int k = 0; k < count; ++k)
     if (!is_permutation(p + (size_t)k * n, n, seen)) return QAP_EINVAL;
   QAP_CUDA(cudaSetDevice(ctx->device));
   const size_t pbytes = (size_t)count * n * sizeof(int32_t);
   const size_t off_cost = ((pbytes + 255) / 256) * 256;
-  qap_status st = ensure_scratch(ctx, off_cost + (size_t)count * 8);
-  if (st != QAP_OK) return st;
+  QAP_TRY(grow(&ctx->scratch, &ctx->scratch_bytes, off_cost + (size_t)count * 8));
   char* base = static_cast<char*>(ctx->scratch);
   int32_t* dp = reinterpret_cast<int32_t*>(base);
   int64_t* dc = reinterpret_cast<int64_t*>(base + off_cost);
@@ -470,10 +610,10 @@ qap_status qap_cost(qap_ctx* ctx, int32_t count, const int32_t* p, int64_t* cost
   const int grid = std::min(count, ctx->sms * 8);
   if (ctx->fbytes == 1)
     qapk::cost_kernel<int8_t, 256><<<grid, 256, 0, s>>>(static_cast<const int8_t*>(ctx->dF),
-                                                        ctx->ldF, ctx->dD, n, dp, count, dc);
+                                                        ctx->di.ldF, ctx->dD, n, dp, count, dc);
   else
     qapk::cost_kernel<int16_t, 256><<<grid, 256, 0, s>>>(static_cast<const int16_t*>(ctx->dF),
-                                                         ctx->ldF, ctx->dD, n, dp, count, dc);
+                                                         ctx->di.ldF, ctx->dD, n, dp, count, dc);
   QAP_CUDA(cudaGetLastError());
   QAP_CUDA(cudaMemcpyAsync(cost, dc, (size_t)count * 8, cudaMemcpyDeviceToHost, s));
   QAP_CUDA(cudaStreamSynchronize(s));
@@ -514,6 +654,145 @@ qap_status qap_tabu(qap_ctx* ctx, int32_t starts, int32_t iters, qap_tenure tenu
   o.best_iter = best_iter;
   o.status = status;
   return qap_search(ctx, &p, nullptr, &o);
+}
+
+// ---------------------------------------------------------------------------
+// a batch of instances
+// ---------------------------------------------------------------------------
+
+qap_status qap_batch_create(int32_t count, const int64_t* const* F, const int64_t* const* D,
+                            const int32_t* n, uint32_t flags, qap_batch** out) {
+  if (!out) return QAP_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !F || !D || !n || (flags & ~QAP_FORCE_INT64)) return QAP_EINVAL;
+  qap_batch* b = new (std::nothrow) qap_batch();
+  if (!b) return QAP_ENOMEM;
+  auto fail = [&](qap_status s) {
+    qap_batch_destroy(b);
+    return s;
+  };
+  b->count = count;
+  b->di.resize(count);
+  int64_t maxF = 0, maxB = 0;
+  for (int i = 0; i < count; ++i) {
+    qap_status st = inspect_instance(F[i], D[i], n[i], &b->di[i]);
+    if (st != QAP_OK) return fail(st);
+    maxF = std::max(maxF, b->di[i].maxF);
+    maxB = std::max(maxB, b->di[i].bound);
+    b->nmax = std::max(b->nmax, n[i]);
+  }
+  // one delta width and one flow width for the whole batch
+  b->dbytes = ((flags & QAP_FORCE_INT64) || maxB > (int64_t)INT_MAX - 1) ? 8 : 4;
+  b->fbytes = (maxF <= 127 && b->dbytes == 4) ? 1 : 2;
+  qap_status st = device_attrs(&b->device, &b->sms, &b->smem_optin);
+  if (st != QAP_OK) return fail(st);
+  std::vector<unsigned char> blob;
+  b->offF.resize(count);
+  b->offFt.resize(count);
+  b->offD.resize(count);
+  for (int i = 0; i < count; ++i) {
+    DevInstance& d = b->di[i];
+    d.ldF = pad_ldF(d.n, b->fbytes);
+    d.ldP = pad_ldP(d.n);
+    std::vector<unsigned char> iF, iFt, iD;
+    build_images(F[i], D[i], d, b->fbytes, iF, iFt, iD);
+    auto append = [&](const std::vector<unsigned char>& v) {
+      const size_t off = (blob.size() + 255) / 256 * 256;
+      blob.resize(off + v.size());
+      std::memcpy(blob.data() + off, v.data(), v.size());
+      return off;
+    };
+    b->offF[i] = append(iF);
+    b->offFt[i] = d.symF ? b->offF[i] : append(iFt);
+    b->offD[i] = append(iD);
+  }
+  if (cudaMalloc(&b->data, blob.size()) != cudaSuccess) return fail(QAP_ENOMEM);
+  cudaError_t e = cudaMemcpy(b->data, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
+  if (cudaMalloc(&b->d_insts, sizeof(qapk::InstArgs) * count) != cudaSuccess)
+    return fail(QAP_ENOMEM);
+  if (cudaMalloc(&b->d_counter, 256) != cudaSuccess) return fail(QAP_ENOMEM);
+  e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreateWithFlags"));
+  *out = b;
+  return QAP_OK;
+}
+
+void qap_batch_destroy(qap_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->data) cudaFree(b->data);
+  if (b->d_insts) cudaFree(b->d_insts);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_counter) cudaFree(b->d_counter);
+  if (b->scratch) cudaFree(b->scratch);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+qap_status qap_batch_info(const qap_batch* b, int32_t* count, int32_t* nmax,
+                          int32_t* delta_bytes) {
+  if (!b) return QAP_EINVAL;
+  if (count) *count = b->count;
+  if (nmax) *nmax = b->nmax;
+  if (delta_bytes) *delta_bytes = b->dbytes;
+  return QAP_OK;
+}
+
+qap_status qap_batch_plan(qap_batch* b, const qap_search_params* params, qap_plan_info* out) {
+  if (!b || !out) return QAP_EINVAL;
+  QAP_TRY(validate_params(params));
+  QAP_CUDA(cudaSetDevice(b->device));
+  Launch L;
+  QAP_TRY(plan_batch(b, params, &L));
+  out->threads_per_walk = L.plan.nt;
+  out->pairs_per_thread = L.plan.maxpt;
+  out->smem_bytes = L.smem;
+  out->grid = L.grid;
+  out->ctas_per_sm = L.ctas_per_sm;
+  out->sms = b->sms;
+  return QAP_OK;
+}
+
+qap_status qap_batch_search_async(qap_batch* b, const qap_search_params* params,
+                                  const qap_walk_outputs* out, int32_t p_stride, void* stream) {
+  if (!b) return QAP_EINVAL;
+  QAP_TRY(validate_params(params));
+  if (!out || !out->best_cost || p_stride < b->nmax) return QAP_EINVAL;
+  if (params->launch != QAP_LAUNCH_PERSISTENT) return QAP_EINVAL;
+  QAP_CUDA(cudaSetDevice(b->device));
+  Launch L;
+  QAP_TRY(plan_batch(b, params, &L));
+  QAP_TRY(batch_tables(b, L.plan.nt, params->starts));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int items = b->count * params->starts;
+  qapk::BatchArgs a{};
+  a.insts = b->d_insts;
+  a.item_inst = b->d_items;
+  a.item_walk = b->d_items + items;
+  a.row_base = b->d_items + 2 * (size_t)items;
+  a.items = items;
+  a.counter = b->d_counter;
+  a.s = make_search_args(params, out, p_stride);
+  QAP_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(int), s));
+  const auto fn = reinterpret_cast<qapk::BatchKernelFn>(const_cast<void*>(L.fn));
+  fn<<<L.grid, L.plan.nt, L.smem, s>>>(a);
+  QAP_CUDA(cudaGetLastError());
+  return QAP_OK;
+}
+
+qap_status qap_batch_search(qap_batch* b, const qap_search_params* params,
+                            const qap_walk_outputs* out, int32_t p_stride) {
+  if (!b) return QAP_EINVAL;
+  QAP_TRY(validate_params(params));
+  if (!out || !out->best_cost || p_stride < b->nmax) return QAP_EINVAL;
+  QAP_CUDA(cudaSetDevice(b->device));
+  const int W = b->count * params->starts;
+  const OutLayout L = out_layout(W, p_stride);
+  QAP_TRY(grow(&b->scratch, &b->scratch_bytes, L.total));
+  const qap_walk_outputs d = carve_outputs(static_cast<char*>(b->scratch), L, W);
+  QAP_TRY(qap_batch_search_async(b, params, &d, p_stride, b->stream));
+  return copy_outputs_back(out, d, W, p_stride, b->stream);
 }
 
 }  // extern "C"

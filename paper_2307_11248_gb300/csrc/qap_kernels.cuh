@@ -48,20 +48,24 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kNoMove = 0xffffffffu;
 constexpr int kDescentCap = 1 << 20;      // 2opt moves when no cap is given
 
-struct WalkArgs {
+// One instance as the kernels see it.
+struct InstArgs {
   int n, ldF, ldP;    // ldF: elements per F row; ldP: bytes per P row
   int symF, symD;
   int group;          // lanes per phase-X task (1, 2, 4 or 8)
   const void* F;      // n x ldF (int8 or int16), row-major, zero padded
   const void* Ft;     // transpose of F (== F when symF)
   const int8_t* D;    // n x n, row-major
-  int walks;          // walks processed by this launch
-  int walk_offset;    // index of this launch's first walk in the outputs
-  uint32_t walk_base; // walk id of output row 0
+};
+
+// Search parameters and per-walk outputs (rows indexed by output row).
+struct SearchArgs {
+  uint32_t walk_base; // walk id of a walk = walk_base + its index in its instance
   uint64_t seed;
-  const int32_t* starts;  // (walk_offset + walks) x n, or null
   int descend, max_descent, iters;
   int tmin, tmax, period, aspiration;
+  int tenure_per_n;   // tmin, tmax, period in tenths of the instance's n
+  int p_stride;       // elements per best_p row
   int32_t* best_p;
   int64_t* best_cost;
   int64_t* final_cost;
@@ -71,6 +75,28 @@ struct WalkArgs {
   int32_t* descent_moves;
   uint64_t* hash;
   uint64_t* descent_hash;
+};
+
+// Walks of one instance.
+struct WalkArgs {
+  InstArgs inst;
+  SearchArgs s;
+  int walks;              // walks processed by this launch
+  int walk_offset;        // index of this launch's first walk among the instance's walks
+  const int32_t* starts;  // (walk_offset + walks) x n, or null
+};
+
+// Walks of many instances in one launch: work item i (in longest-first
+// order) is walk item_walk[i] of instance item_inst[i]; its output row is
+// row_base[inst] + walk.  CTAs take items from a device counter.
+struct BatchArgs {
+  const InstArgs* insts;
+  const int32_t* item_inst;
+  const int32_t* item_walk;
+  const int32_t* row_base;
+  int items;
+  int* counter;           // zeroed before the launch
+  SearchArgs s;
 };
 
 // ---------------------------------------------------------------------------
@@ -492,19 +518,40 @@ __host__ __device__ inline int row_segments(int n, int maxpt) {
   return nseg;
 }
 
+struct Segment {
+  int su, sv, slen;  // pairs (su, sv + i), i < slen
+  int wlen;          // longest segment in the warp
+};
+
+template <int MAXPT>
+__device__ __forceinline__ Segment make_segment(int n) {
+  Segment g{0, 1, 0, 0};
+  const int tid = threadIdx.x;
+  int t0 = 0;
+  for (int u = 0; u < n - 1; ++u) {
+    const int len = n - 1 - u;
+    const int ns = (len + MAXPT - 1) / MAXPT;
+    if (tid >= t0 && tid < t0 + ns) {
+      const int j = tid - t0;
+      g.su = u;
+      g.sv = u + 1 + j * MAXPT;
+      g.slen = min(MAXPT, len - j * MAXPT);
+    }
+    t0 += ns;
+  }
+  g.wlen = __reduce_max_sync(kFull, g.slen);
+  return g;
+}
+
 template <typename DT, typename FE, int NT, int MAXPT>
-__global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int n = a.n, ldF = a.ldF, ldP = a.ldP, tid = threadIdx.x, G = a.group;
-  const bool sym = a.symF && a.symD;
-  const bool warp0 = tid < 32;
-  const SmemLayout L = smem_layout(n, ldF, (int)sizeof(FE), ldP, a.symF, a.symD,
+__device__ __forceinline__ WalkSmem<DT, FE> smem_views(unsigned char* smem, const InstArgs& I) {
+  const SmemLayout L = smem_layout(I.n, I.ldF, (int)sizeof(FE), I.ldP, I.symF, I.symD,
                                    (int)sizeof(DT), NT * MAXPT);
   WalkSmem<DT, FE> S;
   S.F = reinterpret_cast<FE*>(smem + L.offF);
-  S.Ft = a.symF ? S.F : reinterpret_cast<FE*>(smem + L.offFt);
+  S.Ft = I.symF ? S.F : reinterpret_cast<FE*>(smem + L.offFt);
   S.P = reinterpret_cast<int8_t*>(smem + L.offP);
-  S.Pt = a.symD ? S.P : reinterpret_cast<int8_t*>(smem + L.offPt);
+  S.Pt = I.symD ? S.P : reinterpret_cast<int8_t*>(smem + L.offPt);
   S.tabu = reinterpret_cast<int32_t*>(smem + L.offTabu);
   S.vec = smem + L.offVec;
   S.R = reinterpret_cast<DT*>(smem + L.offR);
@@ -515,257 +562,301 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
   S.redD = reinterpret_cast<DT*>(smem + L.offRedD);
   S.redK = reinterpret_cast<uint32_t*>(smem + L.offRedK);
   S.sum = reinterpret_cast<int64_t*>(smem + L.offSum);
+  return S;
+}
 
-  // This thread's row segment: pairs (su, sv + i), i < slen.
-  int su = 0, sv = 1, slen = 0;
-  {
-    int t0 = 0;
-    for (int u = 0; u < n - 1; ++u) {
-      const int len = n - 1 - u;
-      const int ns = (len + MAXPT - 1) / MAXPT;
-      if (tid >= t0 && tid < t0 + ns) {
-        const int j = tid - t0;
-        su = u;
-        sv = u + 1 + j * MAXPT;
-        slen = min(MAXPT, len - j * MAXPT);
-      }
-      t0 += ns;
-    }
+// F (and F^T) into shared memory (rows are whole 16-byte vectors, zero
+// padded); P (and P^T) zeroed so their padding columns stay zero.  Ends with
+// a barrier.
+template <typename DT, typename FE, int NT>
+__device__ __forceinline__ void load_instance(const WalkSmem<DT, FE>& S, const InstArgs& I) {
+  const int tid = threadIdx.x;
+  const int nvec = I.n * I.ldF * (int)sizeof(FE) / 16;
+  const int4* gF = reinterpret_cast<const int4*>(I.F);
+  int4* sF = reinterpret_cast<int4*>(S.F);
+  for (int i = tid; i < nvec; i += NT) sF[i] = gF[i];
+  if (!I.symF) {
+    const int4* gFt = reinterpret_cast<const int4*>(I.Ft);
+    int4* sFt = reinterpret_cast<int4*>(S.Ft);
+    for (int i = tid; i < nvec; i += NT) sFt[i] = gFt[i];
   }
-  // slots past the longest segment of the warp are skipped by the whole warp
-  const int wlen = __reduce_max_sync(kFull, slen);
+  const int pvec = I.n * I.ldP / 16;
+  int4* sP = reinterpret_cast<int4*>(S.P);
+  for (int i = tid; i < pvec; i += NT) sP[i] = make_int4(0, 0, 0, 0);
+  if (!I.symD) {
+    int4* sPt = reinterpret_cast<int4*>(S.Pt);
+    for (int i = tid; i < pvec; i += NT) sPt[i] = make_int4(0, 0, 0, 0);
+  }
+  __syncthreads();
+}
+
+// One whole walk: start permutation, P, Eq. 1, the initial deltas, the 2opt
+// descent, the tabu iterations and the outputs (row `row`).  `wid` is the
+// walk id of the random draws; `start` a given start permutation or null.
+// Starts and ends with every thread of the CTA together.
+template <typename DT, typename FE, int NT, int MAXPT>
+__device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstArgs& I,
+                                         const Segment& seg, const SearchArgs& a, int row,
+                                         uint32_t wid, const int32_t* start) {
+  const int n = I.n, ldF = I.ldF, ldP = I.ldP, tid = threadIdx.x, G = I.group;
+  const bool sym = I.symF && I.symD;
+  const bool warp0 = tid < 32;
+  const int su = seg.su, sv = seg.sv, slen = seg.slen, wlen = seg.wlen;
   const uint32_t ukey = (uint32_t)su << 8;
 
-  // F (and F^T) once per CTA (rows are whole 16-byte vectors, zero padded);
-  // P (and P^T) zeroed once so their padding columns stay zero.
-  {
-    const int nvec = n * ldF * (int)sizeof(FE) / 16;
-    const int4* gF = reinterpret_cast<const int4*>(a.F);
-    int4* sF = reinterpret_cast<int4*>(S.F);
-    for (int i = tid; i < nvec; i += NT) sF[i] = gF[i];
-    if (!a.symF) {
-      const int4* gFt = reinterpret_cast<const int4*>(a.Ft);
-      int4* sFt = reinterpret_cast<int4*>(S.Ft);
-      for (int i = tid; i < nvec; i += NT) sFt[i] = gFt[i];
-    }
-    const int pvec = n * ldP / 16;
-    int4* sP = reinterpret_cast<int4*>(S.P);
-    for (int i = tid; i < pvec; i += NT) sP[i] = make_int4(0, 0, 0, 0);
-    if (!a.symD) {
-      int4* sPt = reinterpret_cast<int4*>(S.Pt);
-      for (int i = tid; i < pvec; i += NT) sPt[i] = make_int4(0, 0, 0, 0);
+  // Start permutation: given, or Fisher-Yates on stream 0.
+  if (start) {
+    for (int x = tid; x < n; x += NT) S.perm[x] = start[x];
+  } else if (tid == 0) {
+    for (int x = 0; x < n; ++x) S.perm[x] = x;
+    Philox4 blk{};
+    for (int i = n - 1; i >= 1; --i) {
+      const uint32_t idx = (uint32_t)(n - 1 - i);
+      if ((idx & 3u) == 0)
+        blk = philox4x32_10(wid, 0u, idx >> 2, 0u, (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+      const int j = (int)below(blk.v[idx & 3u], (uint32_t)(i + 1));
+      const int32_t t = S.perm[i];
+      S.perm[i] = S.perm[j];
+      S.perm[j] = t;
     }
   }
   __syncthreads();
 
-  for (int w = blockIdx.x; w < a.walks; w += gridDim.x) {
-    const int wi = a.walk_offset + w;
-    const uint32_t wid = a.walk_base + (uint32_t)wi;
+  // P = D[p][p] (and its transpose) gathered from global memory.
+  for (int c = tid; c < n * n; c += NT) {
+    const int i = c / n, j = c - (c / n) * n;
+    const int8_t v = I.D[(size_t)S.perm[i] * n + S.perm[j]];
+    S.P[i * ldP + j] = v;
+    if (!I.symD) S.Pt[j * ldP + i] = v;
+  }
+  for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
+  __syncthreads();
 
-    // Start permutation: given, or Fisher-Yates on stream 0.
-    if (a.starts) {
-      for (int x = tid; x < n; x += NT) S.perm[x] = a.starts[(size_t)wi * n + x];
-    } else if (tid == 0) {
-      for (int x = 0; x < n; ++x) S.perm[x] = x;
-      Philox4 blk{};
-      for (int i = n - 1; i >= 1; --i) {
-        const uint32_t idx = (uint32_t)(n - 1 - i);
-        if ((idx & 3u) == 0)
-          blk = philox4x32_10(wid, 0u, idx >> 2, 0u, (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-        const int j = (int)below(blk.v[idx & 3u], (uint32_t)(i + 1));
-        const int32_t t = S.perm[i];
-        S.perm[i] = S.perm[j];
-        S.perm[j] = t;
-      }
-    }
-    __syncthreads();
+  // Eq. 1, g, and the initial deltas of the owned pairs (Eq. 2, O(n) each).
+  int64_t c0 = 0;
+  for (int c = tid; c < n * n; c += NT) {
+    const int i = c / n, j = c - (c / n) * n;
+    c0 += (int64_t)S.F[i * ldF + j] * (int64_t)S.P[i * ldP + j];
+  }
+  c0 = block_sum<NT>(c0, S.sum);
+  compute_g<DT, FE, NT>(S, S.g0, n, ldF, ldP, sym, G);
+  DT dl[MAXPT];
+#pragma unroll
+  for (int i = 0; i < MAXPT; ++i) {
+    dl[i] = DeltaMax<DT>::v;
+    if (i < slen) dl[i] = delta_serial<DT, FE>(S, n, ldF, ldP, sym, su, sv + i);
+    S.tabu[i * NT + tid] = 0;
+  }
 
-    // P = D[p][p] (and its transpose) gathered from global memory.
-    for (int c = tid; c < n * n; c += NT) {
-      const int i = c / n, j = c - (c / n) * n;
-      const int8_t v = a.D[(size_t)S.perm[i] * n + S.perm[j]];
-      S.P[i * ldP + j] = v;
-      if (!a.symD) S.Pt[j * ldP + i] = v;
-    }
-    for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
-    __syncthreads();
+  DT cur = (DT)c0;
+  DT* gc = S.g0;
+  DT* gn = S.g1;
+  uint64_t h = 14695981039346656037ull, dh = h;
+  int dmoves = 0;
 
-    // Eq. 1, g, and the initial deltas of the owned pairs (Eq. 2, O(n) each).
-    int64_t c0 = 0;
-    for (int c = tid; c < n * n; c += NT) {
-      const int i = c / n, j = c - (c / n) * n;
-      c0 += (int64_t)S.F[i * ldF + j] * (int64_t)S.P[i * ldP + j];
-    }
-    c0 = block_sum<NT>(c0, S.sum);
-    compute_g<DT, FE, NT>(S, S.g0, n, ldF, ldP, sym, G);
-    DT dl[MAXPT];
+  // Owners' pass after move (r, s): new deltas, then the scan for the next
+  // iteration `nit` (tabu phase) or the next descent step.  Branch-free per
+  // slot so the shared-memory loads of all slots are in flight together.
+  auto update_and_scan = [&](int r, int s, bool tabu, int nit, int stamp, DT ncur, DT nbest,
+                             DT& bd, uint32_t& bk) {
+    using VO = VecOps<FE>;
+    const auto* vec = reinterpret_cast<const typename VO::V*>(S.vec);
+    const DT gr = gn[r], gs = gn[s];
+    const bool tu = (su == r) | (su == s);        // every pair of the segment touches
+    const int ubase = su == r ? 0 : n;
+    const DT gu = su == r ? gr : gs;
+    int ua, ub, uc, ue;
+    VO::unpack(vec[su], ua, ub, uc, ue);
+    bd = DeltaMax<DT>::v;
+    bk = kNoMove;
 #pragma unroll
     for (int i = 0; i < MAXPT; ++i) {
-      dl[i] = DeltaMax<DT>::v;
-      if (i < slen) dl[i] = delta_serial<DT, FE>(S, n, ldF, ldP, sym, su, sv + i);
-      S.tabu[i * NT + tid] = 0;
-    }
-
-    DT cur = (DT)c0;
-    DT* gc = S.g0;
-    DT* gn = S.g1;
-    uint64_t h = 14695981039346656037ull, dh = h;
-    int dmoves = 0;
-
-    // Owners' pass after move (r, s): new deltas, then the scan for the next
-    // iteration `nit` (tabu phase) or the next descent step.  Branch-free per
-    // slot so the shared-memory loads of all slots are in flight together.
-    auto update_and_scan = [&](int r, int s, bool tabu, int nit, int stamp, DT ncur, DT nbest,
-                               DT& bd, uint32_t& bk) {
-      using VO = VecOps<FE>;
-      const auto* vec = reinterpret_cast<const typename VO::V*>(S.vec);
-      const DT gr = gn[r], gs = gn[s];
-      const bool tu = (su == r) | (su == s);        // every pair of the segment touches
-      const int ubase = su == r ? 0 : n;
-      const DT gu = su == r ? gr : gs;
-      int ua, ub, uc, ue;
-      VO::unpack(vec[su], ua, ub, uc, ue);
-      bd = DeltaMax<DT>::v;
-      bk = kNoMove;
-#pragma unroll
-      for (int i = 0; i < MAXPT; ++i) {
-        if (i >= wlen) break;
-        const bool valid = i < slen;
-        const int v = valid ? sv + i : sv;
-        int va, vb, vc, ve;
-        VO::unpack(vec[v], va, vb, vc, ve);
-        const bool tvr = v == r, tv = tvr | (v == s);
-        const int idx = tu ? ubase + v : (tvr ? 0 : n) + su;  // in range for any v, su
-        const DT rv = S.R[idx];
-        const int tbl = S.tabu[i * NT + tid];
-        const DT gx = tu ? gu : (tvr ? gr : gs);
-        DT d = dl[i];
-        const DT o1 = d + (DT)((ua - va) * (ub - vb) + (uc - vc) * (ue - ve));
-        const bool isrs = (su == r) & (v == s);
-        d = isrs ? -d : (tu | tv) ? rv - gx : o1;
-        d = valid ? d : DeltaMax<DT>::v;
-        dl[i] = d;
-        // the pair just applied carries its new stamp; the store follows the
-        // loop so no shared-memory store sits between the slots' loads
-        const int tb = isrs ? stamp : tbl;
-        const bool adm = !tabu || tb <= nit || (a.aspiration && ncur + d < nbest);
-        if (valid && adm && d < bd) {
-          bd = d;
-          bk = ukey | (uint32_t)v;
-        }
+      if (i >= wlen) break;
+      const bool valid = i < slen;
+      const int v = valid ? sv + i : sv;
+      int va, vb, vc, ve;
+      VO::unpack(vec[v], va, vb, vc, ve);
+      const bool tvr = v == r, tv = tvr | (v == s);
+      const int idx = tu ? ubase + v : (tvr ? 0 : n) + su;  // in range for any v, su
+      const DT rv = S.R[idx];
+      const int tbl = S.tabu[i * NT + tid];
+      const DT gx = tu ? gu : (tvr ? gr : gs);
+      DT d = dl[i];
+      const DT o1 = d + (DT)((ua - va) * (ub - vb) + (uc - vc) * (ue - ve));
+      const bool isrs = (su == r) & (v == s);
+      d = isrs ? -d : (tu | tv) ? rv - gx : o1;
+      d = valid ? d : DeltaMax<DT>::v;
+      dl[i] = d;
+      // the pair just applied carries its new stamp; the store follows the
+      // loop so no shared-memory store sits between the slots' loads
+      const int tb = isrs ? stamp : tbl;
+      const bool adm = !tabu || tb <= nit || (a.aspiration && ncur + d < nbest);
+      if (valid && adm && d < bd) {
+        bd = d;
+        bk = ukey | (uint32_t)v;
       }
-      if (tabu && su == r && s >= sv && s < sv + slen) S.tabu[(s - sv) * NT + tid] = stamp;
-    };
-
-    // ---- 2opt descent (Section 4.1): best move while it improves.
-    if (a.descend) {
-      // A descent strictly lowers the cost at every move, so it ends; the
-      // cap only bounds the kernel's run time on any input.
-      const int cap = a.max_descent >= 0 ? a.max_descent : kDescentCap;
-      DT bd = DeltaMax<DT>::v;
-      uint32_t bk = kNoMove;
-#pragma unroll
-      for (int i = 0; i < MAXPT; ++i)
-        if (i < slen && dl[i] < bd) {
-          bd = dl[i];
-          bk = ukey | (uint32_t)(sv + i);
-        }
-      for (;;) {
-        if (dmoves >= cap) break;
-        block_argmin<DT, NT>(bd, bk, S.redD, S.redK);
-        if (bk == kNoMove || bd >= 0) break;
-        const int r = (int)(bk >> 8), s = (int)(bk & 0xffu);
-        cur += bd;
-        ++dmoves;
-        if (warp0) dh = fnv_step(dh, r, s);
-        phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
-        __syncthreads();
-        update_and_scan(r, s, false, 0, 0, cur, cur, bd, bk);
-        swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, a.symD, r, s);
-        DT* t = gc; gc = gn; gn = t;
-      }
-      __syncthreads();
-      for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
     }
+    if (tabu && su == r && s >= sv && s < sv + slen) S.tabu[(s - sv) * NT + tid] = stamp;
+  };
 
-    // ---- tabu search (Sections 4.3, 4.4).
-    DT best = cur;
-    int best_iter = 0, status = 0, done = 0;
-    bool copy_pending = false;
-    int tenure = 0, tleft = 1;  // period > 0: a new tenure when tleft reaches 0
-    uint32_t tdraw = 0;
+  // ---- 2opt descent (Section 4.1): best move while it improves.
+  if (a.descend) {
+    // A descent strictly lowers the cost at every move, so it ends; the
+    // cap only bounds the kernel's run time on any input.
+    const int cap = a.max_descent >= 0 ? a.max_descent : kDescentCap;
     DT bd = DeltaMax<DT>::v;
     uint32_t bk = kNoMove;
-    if (a.iters > 0) {
 #pragma unroll
-      for (int i = 0; i < MAXPT; ++i) {
-        const DT d = dl[i];
-        const bool adm = S.tabu[i * NT + tid] <= 1 || (a.aspiration && cur + d < best);
-        if (i < slen && adm && d < bd) {
-          bd = d;
-          bk = ukey | (uint32_t)(sv + i);
-        }
+    for (int i = 0; i < MAXPT; ++i)
+      if (i < slen && dl[i] < bd) {
+        bd = dl[i];
+        bk = ukey | (uint32_t)(sv + i);
       }
-    }
-    for (int it = 1; it <= a.iters; ++it) {
+    for (;;) {
+      if (dmoves >= cap) break;
       block_argmin<DT, NT>(bd, bk, S.redD, S.redK);
-      if (copy_pending) {  // p after the previous iteration's move
-        for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
-        copy_pending = false;
-      }
-      if (bk == kNoMove) {
-        status = 1;
-        break;
-      }
+      if (bk == kNoMove || bd >= 0) break;
       const int r = (int)(bk >> 8), s = (int)(bk & 0xffu);
       cur += bd;
-      done = it;
-      if (warp0) h = fnv_step(h, r, s);
-      if (cur < best) {
-        best = cur;
-        best_iter = it;
-        copy_pending = true;
-      }
-      if (a.period > 0 && --tleft == 0) {  // it = 1, period + 1, ...
-        const uint32_t x = walk_draw(a.seed, wid, 1u, tdraw++);
-        tenure = a.tmin + (int)below(x, (uint32_t)(a.tmax - a.tmin + 1));
-        tleft = a.period;
-      }
+      ++dmoves;
+      if (warp0) dh = fnv_step(dh, r, s);
       phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
       __syncthreads();
-      int stamp = it + tenure;
-      if (a.period == 0 && su == r && s >= sv && s < sv + slen) {
-        // the paper's rule: a fresh tenure per move, drawn by the owner only
-        const uint32_t x = walk_draw(a.seed, wid, 1u, (uint32_t)(it - 1));
-        stamp = it + a.tmin + (int)below(x, (uint32_t)(a.tmax - a.tmin + 1));
-      }
-      update_and_scan(r, s, true, it + 1, stamp, cur, best, bd, bk);
-      swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, a.symD, r, s);
+      update_and_scan(r, s, false, 0, 0, cur, cur, bd, bk);
+      swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
       DT* t = gc; gc = gn; gn = t;
     }
     __syncthreads();
-    if (copy_pending)
-      for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
-    __syncthreads();
+    for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
+  }
 
-    // ---- outputs
-    if (a.best_p)
-      for (int x = tid; x < n; x += NT) a.best_p[(size_t)wi * n + x] = S.best[x];
-    if (tid == 0) {
-      a.best_cost[wi] = (int64_t)best;
-      if (a.final_cost) a.final_cost[wi] = (int64_t)cur;
-      if (a.best_iter) a.best_iter[wi] = best_iter;
-      if (a.iters_done) a.iters_done[wi] = done;
-      if (a.status) a.status[wi] = status;
-      if (a.descent_moves) a.descent_moves[wi] = dmoves;
-      if (a.hash) a.hash[wi] = h;
-      if (a.descent_hash) a.descent_hash[wi] = dh;
+  // ---- tabu search (Sections 4.3, 4.4).
+  int tmin = a.tmin, tmax = a.tmax, period = a.period;
+  if (a.tenure_per_n) {
+    tmin = max(1, a.tmin * n / 10);
+    tmax = max(tmin, (a.tmax * n + 9) / 10);
+    period = a.period * n / 10;
+  }
+  DT best = cur;
+  int best_iter = 0, status = 0, done = 0;
+  bool copy_pending = false;
+  int tenure = 0, tleft = 1;  // period > 0: a new tenure when tleft reaches 0
+  uint32_t tdraw = 0;
+  DT bd = DeltaMax<DT>::v;
+  uint32_t bk = kNoMove;
+  if (a.iters > 0) {
+#pragma unroll
+    for (int i = 0; i < MAXPT; ++i) {
+      const DT d = dl[i];
+      const bool adm = S.tabu[i * NT + tid] <= 1 || (a.aspiration && cur + d < best);
+      if (i < slen && adm && d < bd) {
+        bd = d;
+        bk = ukey | (uint32_t)(sv + i);
+      }
     }
+  }
+  for (int it = 1; it <= a.iters; ++it) {
+    block_argmin<DT, NT>(bd, bk, S.redD, S.redK);
+    if (copy_pending) {  // p after the previous iteration's move
+      for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
+      copy_pending = false;
+    }
+    if (bk == kNoMove) {
+      status = 1;
+      break;
+    }
+    const int r = (int)(bk >> 8), s = (int)(bk & 0xffu);
+    cur += bd;
+    done = it;
+    if (warp0) h = fnv_step(h, r, s);
+    if (cur < best) {
+      best = cur;
+      best_iter = it;
+      copy_pending = true;
+    }
+    if (period > 0 && --tleft == 0) {  // it = 1, period + 1, ...
+      const uint32_t x = walk_draw(a.seed, wid, 1u, tdraw++);
+      tenure = tmin + (int)below(x, (uint32_t)(tmax - tmin + 1));
+      tleft = period;
+    }
+    phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
     __syncthreads();
+    int stamp = it + tenure;
+    if (period == 0 && su == r && s >= sv && s < sv + slen) {
+      // the paper's rule: a fresh tenure per move, drawn by the owner only
+      const uint32_t x = walk_draw(a.seed, wid, 1u, (uint32_t)(it - 1));
+      stamp = it + tmin + (int)below(x, (uint32_t)(tmax - tmin + 1));
+    }
+    update_and_scan(r, s, true, it + 1, stamp, cur, best, bd, bk);
+    swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
+    DT* t = gc; gc = gn; gn = t;
+  }
+  __syncthreads();
+  if (copy_pending)
+    for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
+  __syncthreads();
+
+  // ---- outputs
+  if (a.best_p)
+    for (int x = tid; x < n; x += NT) a.best_p[(size_t)row * a.p_stride + x] = S.best[x];
+  if (tid == 0) {
+    a.best_cost[row] = (int64_t)best;
+    if (a.final_cost) a.final_cost[row] = (int64_t)cur;
+    if (a.best_iter) a.best_iter[row] = best_iter;
+    if (a.iters_done) a.iters_done[row] = done;
+    if (a.status) a.status[row] = status;
+    if (a.descent_moves) a.descent_moves[row] = dmoves;
+    if (a.hash) a.hash[row] = h;
+    if (a.descent_hash) a.descent_hash[row] = dh;
+  }
+  __syncthreads();
+}
+
+// Walks of one instance; CTAs loop over walks.
+template <typename DT, typename FE, int NT, int MAXPT>
+__global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const WalkSmem<DT, FE> S = smem_views<DT, FE, NT, MAXPT>(smem, a.inst);
+  const Segment seg = make_segment<MAXPT>(a.inst.n);
+  load_instance<DT, FE, NT>(S, a.inst);
+  for (int w = blockIdx.x; w < a.walks; w += gridDim.x) {
+    const int wi = a.walk_offset + w;
+    run_walk<DT, FE, NT, MAXPT>(S, a.inst, seg, a.s, wi, a.s.walk_base + (uint32_t)wi,
+                                a.starts ? a.starts + (size_t)wi * a.inst.n : nullptr);
+  }
+}
+
+// Walks of many instances; CTAs take (instance, walk) items from a counter
+// and reload F when the instance changes.
+template <typename DT, typename FE, int NT, int MAXPT>
+__global__ void __launch_bounds__(NT, min_blocks(NT)) batch_kernel(const BatchArgs b) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int item_s;
+  int cur_inst = -1;
+  WalkSmem<DT, FE> S{};
+  Segment seg{};
+  InstArgs I{};
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(b.counter, 1);
+    __syncthreads();
+    const int item = item_s;
+    __syncthreads();
+    if (item >= b.items) break;
+    const int inst = b.item_inst[item], w = b.item_walk[item];
+    if (inst != cur_inst) {
+      I = b.insts[inst];
+      S = smem_views<DT, FE, NT, MAXPT>(smem, I);
+      seg = make_segment<MAXPT>(I.n);
+      load_instance<DT, FE, NT>(S, I);
+      cur_inst = inst;
+    }
+    run_walk<DT, FE, NT, MAXPT>(S, I, seg, b.s, b.row_base[inst] + w, b.s.walk_base + (uint32_t)w,
+                                nullptr);
   }
 }
 
 using WalkKernelFn = void (*)(const WalkArgs);
+using BatchKernelFn = void (*)(const BatchArgs);
 
 // ---------------------------------------------------------------------------
 // Eq. 1 for a batch of permutations: one CTA per permutation.

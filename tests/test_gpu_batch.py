@@ -1,0 +1,149 @@
+"""GPU parity of the batched form: many instances of uneven n in one
+persistent launch.  Each instance's walks must equal the oracle's walks of
+that instance alone (same walk ids), bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2307_11248_gb300 as q
+from paper_2307_11248_gb300 import instances
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ["best_cost", "final_cost", "best_iter", "iters_done", "status", "descent_moves",
+          "hash", "descent_hash"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test selected but no CUDA device is available")
+    oracle.build()
+    q.lib()
+    return torch
+
+
+def check_instance(g, inst_idx, W, F, D, **kw):
+    n = F.shape[0]
+    rows = slice(inst_idx * W, (inst_idx + 1) * W)
+    o = oracle.run_walks(F, D, W, walk_ids=np.arange(W), **kw)
+    for k in FIELDS:
+        assert np.array_equal(g[k][rows].astype(np.int64), o[k].astype(np.int64)), (inst_idx, k)
+    assert np.array_equal(g["best_p"][rows, :n], o["best_p"]), (inst_idx, "best_p")
+
+
+def test_lognormal_batch_int64_bit_exact():
+    insts = instances.batch_instances(10, 3)
+    W, iters = 4, 300
+    with q.Batch([i.F for i in insts], [i.D for i in insts], force_int64=True) as b:
+        assert b.info["delta_bytes"] == 8 and b.info["count"] == 10
+        tn = (20, 40, 60)
+        g = b.search(q.make_params(W, seed=1004, iters=iters, tenure=tn))
+    for i, inst in enumerate(insts):
+        check_instance(g, i, W, inst.F, inst.D, seed=1004, iters=iters, tenure=tn)
+
+
+def test_uniform_batch_int8_descend_then_tabu():
+    Fs, Ds = [], []
+    for k, n in enumerate([12, 37, 50, 23, 64, 9]):
+        F, D = instances.uniform_instance(n, 50 + k, symmetric=(k % 2 == 0))
+        Fs.append(F)
+        Ds.append(D)
+    W = 5
+    with q.Batch(Fs, Ds) as b:
+        assert b.info["delta_bytes"] == 4
+        g = b.search(q.make_params(W, seed=7, iters=250, tenure=(5, 15, 30), descend=True))
+    for i in range(len(Fs)):
+        check_instance(g, i, W, Fs[i], Ds[i], seed=7, iters=250, tenure=(5, 15, 30),
+                       descend=True)
+
+
+def test_tenure_per_n_matches_each_instance_rule():
+    Fs, Ds = [], []
+    for k, n in enumerate([20, 33, 47]):
+        F, D = instances.uniform_instance(n, 70 + k, symmetric=False)
+        Fs.append(F)
+        Ds.append(D)
+    W = 3
+    with q.Batch(Fs, Ds) as b:
+        g = b.search(q.make_params(W, seed=8, iters=300, tenure=(9, 11, 20), tenure_per_n=True))
+    for i in range(3):
+        check_instance(g, i, W, Fs[i], Ds[i], seed=8, iters=300,
+                       tenure=instances.baseline_tenure(Fs[i].shape[0]))
+
+
+def test_batch_equals_single_instance_searches():
+    Fs, Ds = [], []
+    for k, n in enumerate([30, 45, 20]):
+        F, D = instances.lognormal_instance(n, 90 + k, symmetric=False)
+        Fs.append(F)
+        Ds.append(D)
+    W = 6
+    prm = q.make_params(W, seed=3, iters=400, tenure=(4, 12, 0), walk_base=17)
+    with q.Batch(Fs, Ds, force_int64=True) as b:
+        g = b.search(prm)
+    for i in range(3):
+        with q.Instance(Fs[i], Ds[i], force_int64=True) as inst:
+            s = inst.search(prm)
+        for k in FIELDS:
+            assert np.array_equal(g[k][i * W:(i + 1) * W], s[k]), (i, k)
+        assert np.array_equal(g["best_p"][i * W:(i + 1) * W, :Fs[i].shape[0]], s["best_p"])
+
+
+def test_batch_async_in_cuda_graph(gpu):
+    torch = gpu
+    insts = instances.batch_instances(6, 11)
+    W = 3
+    prm = q.make_params(W, seed=5, iters=200, tenure=(10, 20, 40))
+    with q.Batch([i.F for i in insts], [i.D for i in insts], force_int64=True) as b:
+        outs = b.device_outputs(W)
+        s = torch.cuda.Stream()
+        b.search_async(prm, outs, stream=s)  # first call writes the tables
+        s.synchronize()
+        first = {k: v.clone() for k, v in outs.items()}
+        for v in outs.values():
+            v.zero_()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            b.search_async(prm, outs, stream=s)
+        graph.replay()
+        graph.replay()
+        torch.cuda.synchronize()
+        for k in outs:
+            assert torch.equal(outs[k], first[k]), k
+    g = {k: v.cpu().numpy() for k, v in first.items()}
+    g["hash"] = g["hash"].view(np.uint64)
+    g["descent_hash"] = g["descent_hash"].view(np.uint64)
+    for i, inst in enumerate(insts):
+        check_instance(g, i, W, inst.F, inst.D, seed=5, iters=200, tenure=(10, 20, 40))
+
+
+def test_full_batch512_sampled_walks():
+    """The full workload (512 instances, n in [20, 150], 64 walks x 5000
+    iterations, int64) in one persistent launch; sampled walks of sampled
+    instances checked against the oracle, every walk checked for a valid
+    permutation and its Eq. 1 cost."""
+    w = instances.workload_batch512()
+    insts = w["instances"]
+    W, iters = w["walks"], w["iters"]
+    # each instance's own tenure rule: [0.9n, 1.1n] redrawn every 2n
+    with q.Batch([i.F for i in insts], [i.D for i in insts], force_int64=True) as b:
+        g = b.search(q.make_params(W, seed=w["seed"], iters=iters, tenure=(9, 11, 20),
+                                   tenure_per_n=True))
+    assert (g["iters_done"] == iters).all() and (g["status"] == 0).all()
+    rng = np.random.default_rng(0)
+    for i in rng.choice(len(insts), size=3, replace=False):
+        inst = insts[i]
+        rows = [int(i * W + k) for k in (0, W - 1)]
+        o = oracle.run_walks(inst.F, inst.D, 2, seed=w["seed"], iters=iters,
+                             tenure=instances.baseline_tenure(inst.n), walk_ids=np.array([0, W - 1]))
+        for k in FIELDS:
+            assert np.array_equal(g[k][rows].astype(np.int64), o[k].astype(np.int64)), (i, k)
+        assert np.array_equal(g["best_p"][rows, :inst.n], o["best_p"])
+    for i in rng.choice(len(insts), size=20, replace=False):
+        inst = insts[i]
+        P = g["best_p"][i * W:(i + 1) * W, :inst.n]
+        assert (np.sort(P, axis=1) == np.arange(inst.n)).all()
+        with q.Instance(inst.F, inst.D, force_int64=True) as one:
+            assert np.array_equal(one.cost(P), g["best_cost"][i * W:(i + 1) * W])
