@@ -258,6 +258,34 @@ qap_status qap_batch_search(qap_batch* b, const qap_search_params* params,
 qap_status qap_batch_search_async(qap_batch* b, const qap_search_params* params,
                                   const qap_walk_outputs* out, int32_t p_stride, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batch search that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when
+ * they search, for example a host runtime whose own allocator owns all
+ * device memory, or code on a latency-critical path where a cudaMalloc (and
+ * the device-wide synchronisation it can cause) is not allowed.
+ *
+ * Same arguments, results and errors as qap_batch_search_async (device
+ * outputs, stream-ordered kernel launch), but the work-queue counter, the
+ * instance table and the item lists live in one static device array of
+ * about 1 MiB compiled into the library, held by every GPU that loads the
+ * library until the process exits.  The call performs no cudaMalloc,
+ * cudaFree or other allocating routine, on the device or on the host.
+ *
+ * Limits: at most 4096 instances and at most 65536 walks in total
+ * (count x params->starts); larger calls return QAP_EINVAL and
+ * qap_last_error() says which limit was exceeded.
+ *
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Every call reuses the same array and leaves its tables in it: the call
+ * rewrites the tables and zeroes the counter before its kernel starts, so
+ * two calls whose kernels overlap on the GPU race on the array; order them
+ * on one stream or synchronise between them.  The call copies its tables
+ * from static host memory, so it may wait until the stream reaches them. */
+qap_status qap_batch_search_noalloc(qap_batch* b, const qap_search_params* params,
+                                    const qap_walk_outputs* out, int32_t p_stride, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

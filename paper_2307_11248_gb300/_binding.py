@@ -117,6 +117,9 @@ def lib():
             L.qap_batch_search_async.argtypes = [vp, ctypes.POINTER(SearchParams),
                                                  ctypes.POINTER(WalkOutputs), i32, vp]
             L.qap_batch_search_async.restype = st
+            L.qap_batch_search_noalloc.argtypes = [vp, ctypes.POINTER(SearchParams),
+                                                   ctypes.POINTER(WalkOutputs), i32, vp]
+            L.qap_batch_search_noalloc.restype = st
             _lib = L
     return _lib
 
@@ -346,6 +349,15 @@ def qap_batch_search_async(h, params, d_out, p_stride, stream):
     _check(lib().qap_batch_search_async(h, ctypes.byref(params), ctypes.byref(o), p_stride,
                                         ctypes.c_void_p(int(stream or 0))),
            "qap_batch_search_async")
+
+
+def qap_batch_search_noalloc(h, params, d_out, p_stride, stream):
+    """qap_batch_search_async without any allocation inside the call (its
+    work queue and tables live in a static device array); see qap.h."""
+    o = WalkOutputs(**{k: int(d_out.get(k, 0) or 0) for k in OUTPUT_FIELDS})
+    _check(lib().qap_batch_search_noalloc(h, ctypes.byref(params), ctypes.byref(o), p_stride,
+                                          ctypes.c_void_p(int(stream or 0))),
+           "qap_batch_search_noalloc")
 
 
 class Batch:

@@ -796,3 +796,125 @@ qap_status qap_batch_search(qap_batch* b, const qap_search_params* params,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batch search without device allocation.
+//
+// The work-queue counter, the instance table and the item lists of
+// qap_batch_search_noalloc live in one file-scope device array instead of
+// memory from cudaMalloc.  Every GPU that loads the library holds the array
+// (kNoallocBytes) until the process exits.  In host code the array's name
+// stands for a host-side shadow, so its device address is looked up once per
+// device with cudaGetSymbolAddress and that address is what the kernels get.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoallocMaxInstances = 4096;
+constexpr int kNoallocMaxItems = 65536;
+constexpr size_t kNoallocInstOff = 256;  // counter in the first 256 bytes
+constexpr size_t kNoallocItemsOff =
+    kNoallocInstOff + (sizeof(qapk::InstArgs) * kNoallocMaxInstances + 255) / 256 * 256;
+constexpr size_t kNoallocBytes =
+    kNoallocItemsOff + sizeof(int32_t) * (2 * (size_t)kNoallocMaxItems + kNoallocMaxInstances);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Host staging of the tables (static storage: the call allocates no host
+// memory either).  Calls serialise on g_noalloc_mu while they use it; a copy
+// from pageable host memory has read its source when cudaMemcpyAsync
+// returns, so the next call may overwrite the staging.
+qapk::InstArgs g_noalloc_h_insts[kNoallocMaxInstances];
+int32_t g_noalloc_h_items[2 * kNoallocMaxItems + kNoallocMaxInstances];
+int32_t g_noalloc_h_order[kNoallocMaxInstances];
+int32_t g_noalloc_h_bucket[kMaxN + 2];
+
+// Device address of the array on the current device (set-up on first use).
+qap_status noalloc_scratch(int device, unsigned char** out) {
+  if (device < 0 || device >= kNoallocMaxDevices) return QAP_EUNSUPPORTED;
+  if (!g_noalloc_addr[device]) {
+    void* ptr = nullptr;
+    QAP_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_addr[device] = static_cast<unsigned char*>(ptr);
+  }
+  *out = g_noalloc_addr[device];
+  return QAP_OK;
+}
+
+}  // namespace
+
+extern "C" qap_status qap_batch_search_noalloc(qap_batch* b, const qap_search_params* params,
+                                               const qap_walk_outputs* out, int32_t p_stride,
+                                               void* stream) {
+  if (!b) return QAP_EINVAL;
+  QAP_TRY(validate_params(params));
+  if (!out || !out->best_cost || p_stride < b->nmax) return QAP_EINVAL;
+  if (params->launch != QAP_LAUNCH_PERSISTENT) return QAP_EINVAL;
+  const int64_t items = (int64_t)b->count * params->starts;
+  if (b->count > kNoallocMaxInstances || items > kNoallocMaxItems) {
+    snprintf(g_last_error, sizeof(g_last_error),
+             "qap_batch_search_noalloc: %d instances x %d walks exceeds the static scratch "
+             "limit of %d instances and %d walks in total",
+             b->count, params->starts, kNoallocMaxInstances, kNoallocMaxItems);
+    return QAP_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  QAP_CUDA(cudaSetDevice(b->device));
+  unsigned char* base = nullptr;
+  QAP_TRY(noalloc_scratch(b->device, &base));
+  Launch L;
+  QAP_TRY(plan_batch(b, params, &L));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int count = b->count, W = params->starts;
+
+  // instance table for this plan's thread count
+  char* data = static_cast<char*>(b->data);
+  for (int i = 0; i < count; ++i)
+    g_noalloc_h_insts[i] = inst_args(b->di[i], data + b->offF[i], data + b->offFt[i],
+                                     reinterpret_cast<int8_t*>(data + b->offD[i]), L.plan.nt,
+                                     b->fbytes);
+  // items, longest instances first (stable counting sort by n)
+  for (int v = 0; v <= kMaxN + 1; ++v) g_noalloc_h_bucket[v] = 0;
+  for (int i = 0; i < count; ++i) ++g_noalloc_h_bucket[b->di[i].n];
+  int pos = 0;
+  for (int v = kMaxN; v >= 0; --v) {
+    const int c = g_noalloc_h_bucket[v];
+    g_noalloc_h_bucket[v] = pos;
+    pos += c;
+  }
+  for (int i = 0; i < count; ++i) g_noalloc_h_order[g_noalloc_h_bucket[b->di[i].n]++] = i;
+  int32_t* h_inst = g_noalloc_h_items;
+  int32_t* h_walk = g_noalloc_h_items + items;
+  int32_t* h_row = g_noalloc_h_items + 2 * items;
+  int64_t k = 0;
+  for (int j = 0; j < count; ++j)
+    for (int w = 0; w < W; ++w, ++k) {
+      h_inst[k] = g_noalloc_h_order[j];
+      h_walk[k] = w;
+    }
+  for (int i = 0; i < count; ++i) h_row[i] = i * W;
+
+  int* d_counter = reinterpret_cast<int*>(base);
+  qapk::InstArgs* d_insts = reinterpret_cast<qapk::InstArgs*>(base + kNoallocInstOff);
+  int32_t* d_items = reinterpret_cast<int32_t*>(base + kNoallocItemsOff);
+  QAP_CUDA(cudaMemcpyAsync(d_insts, g_noalloc_h_insts, sizeof(qapk::InstArgs) * count,
+                           cudaMemcpyHostToDevice, s));
+  QAP_CUDA(cudaMemcpyAsync(d_items, g_noalloc_h_items, sizeof(int32_t) * (2 * items + count),
+                           cudaMemcpyHostToDevice, s));
+  QAP_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
+  qapk::BatchArgs a{};
+  a.insts = d_insts;
+  a.item_inst = d_items;
+  a.item_walk = d_items + items;
+  a.row_base = d_items + 2 * items;
+  a.items = (int)items;
+  a.counter = d_counter;
+  a.s = make_search_args(params, out, p_stride);
+  const auto fn = reinterpret_cast<qapk::BatchKernelFn>(const_cast<void*>(L.fn));
+  fn<<<L.grid, L.plan.nt, L.smem, s>>>(a);
+  QAP_CUDA(cudaGetLastError());
+  return QAP_OK;
+}

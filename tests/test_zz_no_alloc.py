@@ -1,0 +1,59 @@
+"""The batch entry point that allocates nothing (qap_batch_search_noalloc),
+for callers that cannot allocate device memory when they search: two calls
+in a row, through the C-ABI, must give exactly the results of the ordinary
+batch entry point (integer search, so the bar is equality)."""
+import numpy as np
+import pytest
+
+import paper_2307_11248_gb300 as q
+from paper_2307_11248_gb300 import instances
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.fail("GPU test selected but no CUDA device is available")
+    q.lib()
+    return t
+
+
+def _batch():
+    insts = instances.batch_instances(9, 21)
+    Fs, Ds = [i.F for i in insts], [i.D for i in insts]
+    F, D = instances.uniform_instance(17, 5, symmetric=False)
+    return q.Batch(Fs + [F], Ds + [D], force_int64=True)
+
+
+def test_noalloc_equals_batch_search_on_two_calls(torch):
+    W = 4
+    prm = q.make_params(W, seed=77, iters=300, tenure=(9, 11, 20), tenure_per_n=True,
+                        descend=True)
+    with _batch() as b:
+        stream = torch.cuda.Stream()
+        ref = b.device_outputs(W)
+        b.search_async(prm, ref, stream=stream)
+        stream.synchronize()
+        for call in range(2):
+            outs = b.device_outputs(W)
+            q.qap_batch_search_noalloc(b.h, prm, {k: v.data_ptr() for k, v in outs.items()},
+                                       b.p_stride, stream.cuda_stream)
+            stream.synchronize()
+            for k in ref:
+                assert torch.equal(outs[k], ref[k]), (call, k)
+        assert (ref["iters_done"] == 300).all()
+
+
+def test_noalloc_rejects_sizes_beyond_its_limit(torch):
+    with _batch() as b:
+        prm = q.make_params(10000, seed=1, iters=10, tenure=(1, 2, 0))  # 100000 walks > 65536
+        outs = b.device_outputs(10000)  # valid buffers, though the call must not start
+        stream = torch.cuda.Stream()
+        with pytest.raises(q.QapError) as e:
+            q.qap_batch_search_noalloc(b.h, prm, {k: v.data_ptr() for k, v in outs.items()},
+                                       b.p_stride, stream.cuda_stream)
+        stream.synchronize()
+        assert e.value.status == q.EINVAL
+        assert "static scratch limit" in q.last_error()
