@@ -65,7 +65,7 @@ typedef enum {
   QAP_ENOMEM = 3,        /* device or host allocation failed                   */
   QAP_ECUDA = 4,         /* a CUDA runtime call failed; see qap_last_error()   */
   QAP_ETIMEOUT = 5,      /* a bounded wait ran out (serving loop)              */
-  QAP_EUNSUPPORTED = 6   /* instance outside the kernels' ranges: n > 181,
+  QAP_EUNSUPPORTED = 6   /* instance outside the kernels' ranges: n > 256,
                             F outside int16 or D outside int8                   */
 } qap_status;
 
@@ -95,7 +95,9 @@ typedef struct {
 /* Create a context for one instance.
  *   F, D   host pointers to n*n int64 values, row-major.  Copied; the caller
  *          may free them when the call returns.  F must fit int16 and D int8.
- *   n      2 <= n <= 181.
+ *   n      2 <= n <= 256.  Up to n = 181 a walk keeps its deltas in
+ *          registers; beyond, in a workspace in device memory (allocated by
+ *          the library on first use), with F in shared or global memory.
  *   flags  0 or QAP_FORCE_INT64.
  *   out    receives the context (NULL on error).
  * Uses the CUDA device current at the call for all later calls.
@@ -135,7 +137,8 @@ typedef struct {
   int32_t aspiration;      /* 0 or 1                                         */
   uint64_t seed;           /* Philox key                                     */
   int32_t launch;          /* QAP_LAUNCH_PERSISTENT or QAP_LAUNCH_PLAIN      */
-  int32_t threads_per_walk;/* 0 = automatic; else 128, 256, 512 or 1024      */
+  int32_t threads_per_walk;/* 0 = automatic; else 128, 256, 512 or 1024
+                              (n > 181 always uses 1024)                     */
   int32_t tenure_per_n;    /* 1: tenure.tmin, tmax, period are tenths of each
                               instance's n: tmin' = max(1, floor(tmin n / 10)),
                               tmax' = max(tmin', ceil(tmax n / 10)),
@@ -227,7 +230,7 @@ typedef struct qap_batch qap_batch;  /* opaque: device copies of all instances *
  *   count  number of instances, >= 1.
  *   F, D   host arrays of `count` host pointers; instance i is n[i] x n[i]
  *          int64, row-major, ranges as for qap_create.  Copied.
- *   n      host array of `count` sizes, 2 <= n[i] <= 181.
+ *   n      host array of `count` sizes, 2 <= n[i] <= 256.
  *   flags  0 or QAP_FORCE_INT64.  One delta width serves the whole batch:
  *          int64 if any instance needs it.
  * Errors: as qap_create, for the first instance that fails. */

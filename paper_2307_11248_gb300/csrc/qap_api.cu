@@ -18,12 +18,12 @@
 #include "qap_kernels.cuh"
 
 namespace qapk {
-WalkKernelFn walk_kernel_i32_f8(int nt, int maxpt);
-WalkKernelFn walk_kernel_i32_f16(int nt, int maxpt);
-WalkKernelFn walk_kernel_i64_f16(int nt, int maxpt);
-BatchKernelFn batch_kernel_i32_f8(int nt, int maxpt);
-BatchKernelFn batch_kernel_i32_f16(int nt, int maxpt);
-BatchKernelFn batch_kernel_i64_f16(int nt, int maxpt);
+WalkKernelFn walk_kernel_i32_f8(int nt, int maxpt, int store);
+WalkKernelFn walk_kernel_i32_f16(int nt, int maxpt, int store);
+WalkKernelFn walk_kernel_i64_f16(int nt, int maxpt, int store);
+BatchKernelFn batch_kernel_i32_f8(int nt, int maxpt, int store);
+BatchKernelFn batch_kernel_i32_f16(int nt, int maxpt, int store);
+BatchKernelFn batch_kernel_i64_f16(int nt, int maxpt, int store);
 }  // namespace qapk
 
 namespace {
@@ -47,23 +47,27 @@ qap_status cuda_fail(cudaError_t e, const char* where) {
     if (s_ != QAP_OK) return s_;       \
   } while (0)
 
-// Largest n: keys pack (r << 8 | s) and the largest register plan holds the
-// row segments of n = 181 with 1024 threads.
-constexpr int kMaxN = 181;
+// Largest n: keys pack (r << 8 | s) into 16 bits.
+constexpr int kMaxN = 256;
 
 struct Plan {
   int nt;
   int maxpt;
+  int store;  // 0, or qapk::kGlobalDelta [| qapk::kGlobalFlow] (large-n plans)
 };
+
+// The large-n plan: 1024 threads, up to 40 slots each in a global workspace
+// (row_segments(256, 40) = 945).
+constexpr Plan kLargePlan = {1024, 40, qapk::kGlobalDelta};
 
 // Register plans (threads per walk, pair slots per thread) compiled into the
 // library.  A plan fits n when its row segments (qapk::row_segments) number
 // at most its threads.  The automatic choice takes the fewest threads that fit
 // with at most eight slots, else the fewest threads that fit at all; for a
 // given thread count the fewest slots that fit.
-const Plan kPlans[] = {{128, 4},  {128, 12}, {256, 6},  {256, 8},   {512, 4},
-                       {512, 8},  {512, 12}, {1024, 8}, {1024, 12}, {1024, 16},
-                       {1024, 20}};
+const Plan kPlans[] = {{128, 4, 0},   {128, 12, 0},  {256, 6, 0},   {256, 8, 0},
+                       {512, 4, 0},   {512, 8, 0},   {512, 12, 0},  {1024, 8, 0},
+                       {1024, 12, 0}, {1024, 16, 0}, {1024, 20, 0}};
 
 bool plan_for(int n, int nt, Plan* out) {
   for (const Plan& p : kPlans)
@@ -163,15 +167,51 @@ qap_status device_attrs(int* device, int* sms, int* smem_optin) {
 }
 
 qapk::WalkKernelFn pick_walk_kernel(int dbytes, int fbytes, const Plan& p) {
-  if (dbytes == 8) return qapk::walk_kernel_i64_f16(p.nt, p.maxpt);
-  if (fbytes == 1) return qapk::walk_kernel_i32_f8(p.nt, p.maxpt);
-  return qapk::walk_kernel_i32_f16(p.nt, p.maxpt);
+  if (dbytes == 8) return qapk::walk_kernel_i64_f16(p.nt, p.maxpt, p.store);
+  if (fbytes == 1) return qapk::walk_kernel_i32_f8(p.nt, p.maxpt, p.store);
+  return qapk::walk_kernel_i32_f16(p.nt, p.maxpt, p.store);
 }
 
 qapk::BatchKernelFn pick_batch_kernel(int dbytes, int fbytes, const Plan& p) {
-  if (dbytes == 8) return qapk::batch_kernel_i64_f16(p.nt, p.maxpt);
-  if (fbytes == 1) return qapk::batch_kernel_i32_f8(p.nt, p.maxpt);
-  return qapk::batch_kernel_i32_f16(p.nt, p.maxpt);
+  if (dbytes == 8) return qapk::batch_kernel_i64_f16(p.nt, p.maxpt, p.store);
+  if (fbytes == 1) return qapk::batch_kernel_i32_f8(p.nt, p.maxpt, p.store);
+  return qapk::batch_kernel_i32_f16(p.nt, p.maxpt, p.store);
+}
+
+// Shared memory of a plan for the instance shapes `d` (the largest over them).
+int plan_smem(const Plan& p, const DevInstance* d, int count, int fbytes, int dbytes) {
+  int smem = 0;
+  for (int i = 0; i < count; ++i)
+    smem = std::max(smem, qapk::smem_layout(d[i].n, d[i].ldF, fbytes, d[i].ldP, d[i].symF,
+                                            d[i].symD, dbytes, p.nt * p.maxpt, p.store)
+                              .bytes);
+  return smem;
+}
+
+// A register plan when one holds n and fits shared memory; else the large-n
+// plan, with F in global memory when it does not fit shared memory either.
+bool choose_plan_fit(int nmax, int threads, const DevInstance* d, int count, int fbytes,
+                     int dbytes, int smem_optin, int reserve, Plan* out) {
+  Plan p;
+  if (nmax <= 181 && choose_plan(nmax, threads, &p) &&
+      plan_smem(p, d, count, fbytes, dbytes) + reserve <= smem_optin) {
+    *out = p;
+    return true;
+  }
+  if (threads != 0 && threads != kLargePlan.nt) return false;
+  if (qapk::row_segments(nmax, kLargePlan.maxpt) > kLargePlan.nt) return false;
+  p = kLargePlan;
+  if (plan_smem(p, d, count, fbytes, dbytes) + reserve > smem_optin)
+    p.store |= qapk::kGlobalFlow;
+  if (plan_smem(p, d, count, fbytes, dbytes) + reserve > smem_optin) return false;
+  *out = p;
+  return true;
+}
+
+size_t workspace_per_cta(const Plan& p, int dbytes) {
+  if (!(p.store & qapk::kGlobalDelta)) return 0;
+  const size_t b = (size_t)p.nt * p.maxpt * ((size_t)dbytes + 4);
+  return (b + 255) / 256 * 256;
 }
 
 std::mutex g_attr_mu;
@@ -318,6 +358,9 @@ struct qap_ctx {
   // growable device buffer of the blocking entry points
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  // workspace of large-n plans (one slice per CTA of the persistent grid)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
 };
 
 struct qap_batch {
@@ -335,6 +378,8 @@ struct qap_batch {
   cudaStream_t stream = nullptr;
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  void* ws = nullptr;  // workspace of large-n plans
+  size_t ws_bytes = 0;
 };
 
 namespace {
@@ -357,14 +402,12 @@ qap_status occupancy(Launch* L, int sms, int work) {
 }
 
 qap_status plan_ctx(qap_ctx* ctx, const qap_search_params* p, Launch* L) {
-  if (!choose_plan(ctx->di.n, p->threads_per_walk, &L->plan)) return QAP_EUNSUPPORTED;
+  if (!choose_plan_fit(ctx->di.n, p->threads_per_walk, &ctx->di, 1, ctx->fbytes, ctx->dbytes,
+                       ctx->smem_optin, 0, &L->plan))
+    return QAP_EUNSUPPORTED;
   L->fn = reinterpret_cast<const void*>(pick_walk_kernel(ctx->dbytes, ctx->fbytes, L->plan));
   if (!L->fn) return QAP_EUNSUPPORTED;
-  const DevInstance& d = ctx->di;
-  L->smem = qapk::smem_layout(d.n, d.ldF, ctx->fbytes, d.ldP, d.symF, d.symD, ctx->dbytes,
-                              L->plan.nt * L->plan.maxpt)
-                .bytes;
-  if (L->smem > ctx->smem_optin) return QAP_EUNSUPPORTED;
+  L->smem = plan_smem(L->plan, &ctx->di, 1, ctx->fbytes, ctx->dbytes);
   QAP_TRY(prepare_kernel(L->fn, L->smem));
   return occupancy(L, ctx->sms, p->starts);
 }
@@ -385,17 +428,13 @@ qapk::InstArgs inst_args(const DevInstance& d, const void* F, const void* Ft, co
 }
 
 qap_status plan_batch(qap_batch* b, const qap_search_params* p, Launch* L) {
-  if (!choose_plan(b->nmax, p->threads_per_walk, &L->plan)) return QAP_EUNSUPPORTED;
+  // the batch kernel also holds one static int
+  if (!choose_plan_fit(b->nmax, p->threads_per_walk, b->di.data(), b->count, b->fbytes,
+                       b->dbytes, b->smem_optin, 16, &L->plan))
+    return QAP_EUNSUPPORTED;
   L->fn = reinterpret_cast<const void*>(pick_batch_kernel(b->dbytes, b->fbytes, L->plan));
   if (!L->fn) return QAP_EUNSUPPORTED;
-  int smem = 0;
-  for (const DevInstance& d : b->di)
-    smem = std::max(smem, qapk::smem_layout(d.n, d.ldF, b->fbytes, d.ldP, d.symF, d.symD,
-                                            b->dbytes, L->plan.nt * L->plan.maxpt)
-                              .bytes);
-  L->smem = smem;
-  // the batch kernel also holds one static int
-  if (L->smem + 16 > b->smem_optin) return QAP_EUNSUPPORTED;
+  L->smem = plan_smem(L->plan, b->di.data(), b->count, b->fbytes, b->dbytes);
   QAP_TRY(prepare_kernel(L->fn, L->smem));
   return occupancy(L, b->sms, b->count * p->starts);
 }
@@ -507,6 +546,7 @@ void qap_destroy(qap_ctx* ctx) {
   if (ctx->dFt) cudaFree(ctx->dFt);
   if (ctx->dD) cudaFree(ctx->dD);
   if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -552,6 +592,13 @@ qap_status qap_search_async(qap_ctx* ctx, const qap_search_params* params,
   a.starts = d_starts;
   a.walks = params->starts;
   a.walk_offset = 0;
+  a.ws_stride = workspace_per_cta(L.plan, ctx->dbytes);
+  if (a.ws_stride) {
+    // the plain form runs one CTA per launch; launches on one stream share it
+    const int ctas = params->launch == QAP_LAUNCH_PLAIN ? 1 : L.grid;
+    QAP_TRY(grow(&ctx->ws, &ctx->ws_bytes, a.ws_stride * ctas));
+    a.ws = static_cast<unsigned char*>(ctx->ws);
+  }
   const auto fn = reinterpret_cast<qapk::WalkKernelFn>(const_cast<void*>(L.fn));
   if (params->launch == QAP_LAUNCH_PLAIN) {
     a.walks = 1;
@@ -726,6 +773,7 @@ void qap_batch_destroy(qap_batch* b) {
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_counter) cudaFree(b->d_counter);
   if (b->scratch) cudaFree(b->scratch);
+  if (b->ws) cudaFree(b->ws);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -774,6 +822,11 @@ qap_status qap_batch_search_async(qap_batch* b, const qap_search_params* params,
   a.items = items;
   a.counter = b->d_counter;
   a.s = make_search_args(params, out, p_stride);
+  a.ws_stride = workspace_per_cta(L.plan, b->dbytes);
+  if (a.ws_stride) {
+    QAP_TRY(grow(&b->ws, &b->ws_bytes, a.ws_stride * L.grid));
+    a.ws = static_cast<unsigned char*>(b->ws);
+  }
   QAP_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(int), s));
   const auto fn = reinterpret_cast<qapk::BatchKernelFn>(const_cast<void*>(L.fn));
   fn<<<L.grid, L.plan.nt, L.smem, s>>>(a);
@@ -867,6 +920,12 @@ extern "C" qap_status qap_batch_search_noalloc(qap_batch* b, const qap_search_pa
   QAP_TRY(noalloc_scratch(b->device, &base));
   Launch L;
   QAP_TRY(plan_batch(b, params, &L));
+  if (L.plan.store != 0) {
+    snprintf(g_last_error, sizeof(g_last_error),
+             "qap_batch_search_noalloc: n = %d needs the large-n plan, whose workspace is "
+             "allocated; the no-allocation form holds n <= 181", b->nmax);
+    return QAP_EUNSUPPORTED;
+  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int count = b->count, W = params->starts;
 

@@ -1,0 +1,34 @@
+// Instantiations of the walk kernels with int32 deltas and int8 flow storage
+// (one translation unit per combination so they compile in parallel), for
+// a batch of instances (batch_kernel); qap_walk_* holds the one-instance kernels.
+#include "qap_kernels.cuh"
+
+namespace qapk {
+
+#define QAP_PLANS(K)                                             \
+  switch (nt * 1000 + maxpt * 10 + store) {                      \
+    case 128040: return K<DT, FE, 128, 4, 0>;                    \
+    case 128120: return K<DT, FE, 128, 12, 0>;                   \
+    case 256060: return K<DT, FE, 256, 6, 0>;                    \
+    case 256080: return K<DT, FE, 256, 8, 0>;                    \
+    case 512040: return K<DT, FE, 512, 4, 0>;                    \
+    case 512080: return K<DT, FE, 512, 8, 0>;                    \
+    case 512120: return K<DT, FE, 512, 12, 0>;                   \
+    case 1024080: return K<DT, FE, 1024, 8, 0>;                  \
+    case 1024120: return K<DT, FE, 1024, 12, 0>;                 \
+    case 1024160: return K<DT, FE, 1024, 16, 0>;                 \
+    case 1024200: return K<DT, FE, 1024, 20, 0>;                 \
+    case 1024401: return K<DT, FE, 1024, 40, kGlobalDelta>;      \
+    case 1024403: return K<DT, FE, 1024, 40, kGlobalDelta | kGlobalFlow>; \
+    default: return nullptr;                                     \
+  }
+
+BatchKernelFn batch_kernel_i32_f8(int nt, int maxpt, int store) {
+  using DT = int32_t;
+  using FE = int8_t;
+  QAP_PLANS(batch_kernel)
+}
+
+#undef QAP_PLANS
+
+}  // namespace qapk

@@ -81,6 +81,8 @@ struct SearchArgs {
 struct WalkArgs {
   InstArgs inst;
   SearchArgs s;
+  unsigned char* ws;      // large-n plans: per-CTA workspace (deltas, tabu stamps)
+  size_t ws_stride;       // bytes per CTA
   int walks;              // walks processed by this launch
   int walk_offset;        // index of this launch's first walk among the instance's walks
   const int32_t* starts;  // (walk_offset + walks) x n, or null
@@ -97,7 +99,18 @@ struct BatchArgs {
   int items;
   int* counter;           // zeroed before the launch
   SearchArgs s;
+  unsigned char* ws;      // large-n plans: per-CTA workspace (deltas, tabu stamps)
+  size_t ws_stride;       // bytes per CTA
 };
+
+// Where a plan keeps its state.  Register plans hold each thread's deltas in
+// registers and the tabu stamps in shared memory.  Large-n plans (bit
+// kGlobalDelta) keep both in a per-CTA workspace in global memory, read and
+// written coalesced (slot i of thread t at i * NT + t), so that F and P of n
+// up to 256 fit in shared memory; with bit kGlobalFlow they also read F and
+// F^T from global memory (L1-cached), leaving shared memory to P and P^T.
+constexpr int kGlobalDelta = 1;
+constexpr int kGlobalFlow = 2;
 
 // ---------------------------------------------------------------------------
 // shared-memory layout (host and device agree through this function)
@@ -111,11 +124,14 @@ struct SmemLayout {
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
 __host__ __device__ inline SmemLayout smem_layout(int n, int ldF, int fbytes, int ldP, int symF,
-                                                  int symD, int dbytes, int slots) {
+                                                  int symD, int dbytes, int slots,
+                                                  int store = 0) {
   SmemLayout L;
   int o = 0;
-  L.offF = o;    o = align16(o + n * ldF * fbytes);
-  L.offFt = o;   o = symF ? o : align16(o + n * ldF * fbytes);
+  const bool fg = store & kGlobalFlow;
+  if (store & kGlobalDelta) slots = 0;
+  L.offF = o;    o = fg ? o : align16(o + n * ldF * fbytes);
+  L.offFt = o;   o = (symF || fg) ? o : align16(o + n * ldF * fbytes);
   L.offP = o;    o = align16(o + n * ldP);
   L.offPt = o;   o = symD ? o : align16(o + n * ldP);
   L.offTabu = o; o = align16(o + slots * 4);
@@ -543,16 +559,25 @@ __device__ __forceinline__ Segment make_segment(int n) {
   return g;
 }
 
-template <typename DT, typename FE, int NT, int MAXPT>
-__device__ __forceinline__ WalkSmem<DT, FE> smem_views(unsigned char* smem, const InstArgs& I) {
+template <typename DT, typename FE, int NT, int MAXPT, int STORE>
+__device__ __forceinline__ WalkSmem<DT, FE> smem_views(unsigned char* smem, const InstArgs& I,
+                                                       unsigned char* ws) {
   const SmemLayout L = smem_layout(I.n, I.ldF, (int)sizeof(FE), I.ldP, I.symF, I.symD,
-                                   (int)sizeof(DT), NT * MAXPT);
+                                   (int)sizeof(DT), NT * MAXPT, STORE);
   WalkSmem<DT, FE> S;
-  S.F = reinterpret_cast<FE*>(smem + L.offF);
-  S.Ft = I.symF ? S.F : reinterpret_cast<FE*>(smem + L.offFt);
+  if (STORE & kGlobalFlow) {
+    S.F = const_cast<FE*>(reinterpret_cast<const FE*>(I.F));
+    S.Ft = const_cast<FE*>(reinterpret_cast<const FE*>(I.Ft));
+  } else {
+    S.F = reinterpret_cast<FE*>(smem + L.offF);
+    S.Ft = I.symF ? S.F : reinterpret_cast<FE*>(smem + L.offFt);
+  }
   S.P = reinterpret_cast<int8_t*>(smem + L.offP);
   S.Pt = I.symD ? S.P : reinterpret_cast<int8_t*>(smem + L.offPt);
-  S.tabu = reinterpret_cast<int32_t*>(smem + L.offTabu);
+  // workspace: deltas (NT * MAXPT x DT), then tabu stamps (NT * MAXPT x int32)
+  S.tabu = (STORE & kGlobalDelta)
+               ? reinterpret_cast<int32_t*>(ws + (size_t)NT * MAXPT * sizeof(DT))
+               : reinterpret_cast<int32_t*>(smem + L.offTabu);
   S.vec = smem + L.offVec;
   S.R = reinterpret_cast<DT*>(smem + L.offR);
   S.g0 = reinterpret_cast<DT*>(smem + L.offG0);
@@ -568,14 +593,15 @@ __device__ __forceinline__ WalkSmem<DT, FE> smem_views(unsigned char* smem, cons
 // F (and F^T) into shared memory (rows are whole 16-byte vectors, zero
 // padded); P (and P^T) zeroed so their padding columns stay zero.  Ends with
 // a barrier.
-template <typename DT, typename FE, int NT>
+template <typename DT, typename FE, int NT, int STORE>
 __device__ __forceinline__ void load_instance(const WalkSmem<DT, FE>& S, const InstArgs& I) {
   const int tid = threadIdx.x;
   const int nvec = I.n * I.ldF * (int)sizeof(FE) / 16;
   const int4* gF = reinterpret_cast<const int4*>(I.F);
   int4* sF = reinterpret_cast<int4*>(S.F);
-  for (int i = tid; i < nvec; i += NT) sF[i] = gF[i];
-  if (!I.symF) {
+  if (!(STORE & kGlobalFlow))
+    for (int i = tid; i < nvec; i += NT) sF[i] = gF[i];
+  if (!I.symF && !(STORE & kGlobalFlow)) {
     const int4* gFt = reinterpret_cast<const int4*>(I.Ft);
     int4* sFt = reinterpret_cast<int4*>(S.Ft);
     for (int i = tid; i < nvec; i += NT) sFt[i] = gFt[i];
@@ -590,14 +616,35 @@ __device__ __forceinline__ void load_instance(const WalkSmem<DT, FE>& S, const I
   __syncthreads();
 }
 
+// The deltas of a thread's slots: registers, or the CTA's workspace.
+template <typename DT, int NT, int MAXPT, bool GLOBAL>
+struct DeltaSlots;
+
+template <typename DT, int NT, int MAXPT>
+struct DeltaSlots<DT, NT, MAXPT, false> {
+  DT v[MAXPT];
+  __device__ __forceinline__ explicit DeltaSlots(unsigned char*) {}
+  __device__ __forceinline__ DT get(int i) const { return v[i]; }
+  __device__ __forceinline__ void set(int i, DT x) { v[i] = x; }
+};
+
+template <typename DT, int NT, int MAXPT>
+struct DeltaSlots<DT, NT, MAXPT, true> {
+  DT* p;  // slot i at p[i * NT]
+  __device__ __forceinline__ explicit DeltaSlots(unsigned char* ws)
+      : p(reinterpret_cast<DT*>(ws) + threadIdx.x) {}
+  __device__ __forceinline__ DT get(int i) const { return p[(size_t)i * NT]; }
+  __device__ __forceinline__ void set(int i, DT x) { p[(size_t)i * NT] = x; }
+};
+
 // One whole walk: start permutation, P, Eq. 1, the initial deltas, the 2opt
 // descent, the tabu iterations and the outputs (row `row`).  `wid` is the
 // walk id of the random draws; `start` a given start permutation or null.
 // Starts and ends with every thread of the CTA together.
-template <typename DT, typename FE, int NT, int MAXPT>
+template <typename DT, typename FE, int NT, int MAXPT, int STORE>
 __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstArgs& I,
                                          const Segment& seg, const SearchArgs& a, int row,
-                                         uint32_t wid, const int32_t* start) {
+                                         uint32_t wid, const int32_t* start, unsigned char* ws) {
   const int n = I.n, ldF = I.ldF, ldP = I.ldP, tid = threadIdx.x, G = I.group;
   const bool sym = I.symF && I.symD;
   const bool warp0 = tid < 32;
@@ -640,11 +687,11 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   }
   c0 = block_sum<NT>(c0, S.sum);
   compute_g<DT, FE, NT>(S, S.g0, n, ldF, ldP, sym, G);
-  DT dl[MAXPT];
+  DeltaSlots<DT, NT, MAXPT, (STORE & kGlobalDelta) != 0> dl(ws);
 #pragma unroll
   for (int i = 0; i < MAXPT; ++i) {
-    dl[i] = DeltaMax<DT>::v;
-    if (i < slen) dl[i] = delta_serial<DT, FE>(S, n, ldF, ldP, sym, su, sv + i);
+    dl.set(i, i < slen ? delta_serial<DT, FE>(S, n, ldF, ldP, sym, su, sv + i)
+                       : DeltaMax<DT>::v);
     S.tabu[i * NT + tid] = 0;
   }
 
@@ -681,12 +728,12 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       const DT rv = S.R[idx];
       const int tbl = S.tabu[i * NT + tid];
       const DT gx = tu ? gu : (tvr ? gr : gs);
-      DT d = dl[i];
+      DT d = dl.get(i);
       const DT o1 = d + (DT)((ua - va) * (ub - vb) + (uc - vc) * (ue - ve));
       const bool isrs = (su == r) & (v == s);
       d = isrs ? -d : (tu | tv) ? rv - gx : o1;
       d = valid ? d : DeltaMax<DT>::v;
-      dl[i] = d;
+      dl.set(i, d);
       // the pair just applied carries its new stamp; the store follows the
       // loop so no shared-memory store sits between the slots' loads
       const int tb = isrs ? stamp : tbl;
@@ -708,8 +755,8 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     uint32_t bk = kNoMove;
 #pragma unroll
     for (int i = 0; i < MAXPT; ++i)
-      if (i < slen && dl[i] < bd) {
-        bd = dl[i];
+      if (i < slen && dl.get(i) < bd) {
+        bd = dl.get(i);
         bk = ukey | (uint32_t)(sv + i);
       }
     for (;;) {
@@ -747,7 +794,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   if (a.iters > 0) {
 #pragma unroll
     for (int i = 0; i < MAXPT; ++i) {
-      const DT d = dl[i];
+      const DT d = dl.get(i);
       const bool adm = S.tabu[i * NT + tid] <= 1 || (a.aspiration && cur + d < best);
       if (i < slen && adm && d < bd) {
         bd = d;
@@ -813,25 +860,28 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
 }
 
 // Walks of one instance; CTAs loop over walks.
-template <typename DT, typename FE, int NT, int MAXPT>
+template <typename DT, typename FE, int NT, int MAXPT, int STORE>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const WalkSmem<DT, FE> S = smem_views<DT, FE, NT, MAXPT>(smem, a.inst);
+  unsigned char* ws = a.ws ? a.ws + a.ws_stride * blockIdx.x : nullptr;
+  const WalkSmem<DT, FE> S = smem_views<DT, FE, NT, MAXPT, STORE>(smem, a.inst, ws);
   const Segment seg = make_segment<MAXPT>(a.inst.n);
-  load_instance<DT, FE, NT>(S, a.inst);
+  load_instance<DT, FE, NT, STORE>(S, a.inst);
   for (int w = blockIdx.x; w < a.walks; w += gridDim.x) {
     const int wi = a.walk_offset + w;
-    run_walk<DT, FE, NT, MAXPT>(S, a.inst, seg, a.s, wi, a.s.walk_base + (uint32_t)wi,
-                                a.starts ? a.starts + (size_t)wi * a.inst.n : nullptr);
+    run_walk<DT, FE, NT, MAXPT, STORE>(S, a.inst, seg, a.s, wi, a.s.walk_base + (uint32_t)wi,
+                                       a.starts ? a.starts + (size_t)wi * a.inst.n : nullptr,
+                                       ws);
   }
 }
 
 // Walks of many instances; CTAs take (instance, walk) items from a counter
 // and reload F when the instance changes.
-template <typename DT, typename FE, int NT, int MAXPT>
+template <typename DT, typename FE, int NT, int MAXPT, int STORE>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) batch_kernel(const BatchArgs b) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int item_s;
+  unsigned char* ws = b.ws ? b.ws + b.ws_stride * blockIdx.x : nullptr;
   int cur_inst = -1;
   WalkSmem<DT, FE> S{};
   Segment seg{};
@@ -845,13 +895,13 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) batch_kernel(const BatchAr
     const int inst = b.item_inst[item], w = b.item_walk[item];
     if (inst != cur_inst) {
       I = b.insts[inst];
-      S = smem_views<DT, FE, NT, MAXPT>(smem, I);
+      S = smem_views<DT, FE, NT, MAXPT, STORE>(smem, I, ws);
       seg = make_segment<MAXPT>(I.n);
-      load_instance<DT, FE, NT>(S, I);
+      load_instance<DT, FE, NT, STORE>(S, I);
       cur_inst = inst;
     }
-    run_walk<DT, FE, NT, MAXPT>(S, I, seg, b.s, b.row_base[inst] + w, b.s.walk_base + (uint32_t)w,
-                                nullptr);
+    run_walk<DT, FE, NT, MAXPT, STORE>(S, I, seg, b.s, b.row_base[inst] + w,
+                                       b.s.walk_base + (uint32_t)w, nullptr, ws);
   }
 }
 

@@ -52,5 +52,5 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
         q.qap_create(np.zeros((4, 4)), big)
     assert e.value.status == q.EUNSUPPORTED
     with pytest.raises(q.QapError) as e:
-        q.qap_create(np.zeros((200, 200)), np.zeros((200, 200)))
+        q.qap_create(np.zeros((300, 300)), np.zeros((300, 300)))
     assert e.value.status == q.EUNSUPPORTED

@@ -147,3 +147,19 @@ def test_full_batch512_sampled_walks():
         assert (np.sort(P, axis=1) == np.arange(inst.n)).all()
         with q.Instance(inst.F, inst.D, force_int64=True) as one:
             assert np.array_equal(one.cost(P), g["best_cost"][i * W:(i + 1) * W])
+
+
+def test_batch_with_large_instances_uses_workspace():
+    Fs, Ds = [], []
+    for k, n in enumerate([240, 30, 190, 77]):
+        F, D = instances.uniform_instance(n, 500 + k, symmetric=(k % 2 == 0))
+        Fs.append(F)
+        Ds.append(D)
+    W = 2
+    prm = q.make_params(W, seed=4, iters=50, tenure=(9, 11, 20), tenure_per_n=True)
+    with q.Batch(Fs, Ds) as b:
+        assert b.plan(prm)["pairs_per_thread"] == 40
+        g = b.search(prm)
+    for i in range(len(Fs)):
+        check_instance(g, i, W, Fs[i], Ds[i], seed=4, iters=50,
+                       tenure=instances.baseline_tenure(Fs[i].shape[0]))

@@ -173,6 +173,27 @@ def test_signed_values_and_diagonals(n, sym, diag):
     assert_same(g, o)
 
 
+@pytest.mark.parametrize("n,sym,descend", [(200, True, False), (256, True, True),
+                                            (190, False, False), (256, False, True)])
+def test_large_n_global_workspace(n, sym, descend):
+    """n > 181: deltas and tabu stamps in a device workspace; asymmetric
+    n = 256 also reads F from global memory."""
+    F, D = instances.uniform_instance(n, 300 + n, symmetric=sym)
+    iters = 60
+    tn = instances.baseline_tenure(n)
+    g, o, info = run_both(F, D, 3, seed=19, iters=iters, tenure=tn, descend=descend,
+                          max_descent=40)
+    assert_same(g, o)
+    assert (g["iters_done"] == iters).all()
+
+
+def test_large_n_plain_and_persistent_agree():
+    F, D = instances.grid_instance(230, 4)
+    prm = dict(seed=2, iters=40, tenure=(10, 30, 0))
+    g1, o, _ = run_both(F, D, 2, launch=q.LAUNCH_PLAIN, **prm)
+    assert_same(g1, o)
+
+
 def test_force_int64_gives_same_results():
     w = instances.workload_asym50()
     a, o, ia = run_both(w["F"], w["D"], 8, seed=5, iters=700, tenure=w["tenure"])
@@ -232,6 +253,13 @@ def test_given_starts():
     starts = np.stack([rng.permutation(26) for _ in range(5)]).astype(np.int32)
     g, o, _ = run_both(F, D, 5, seed=8, iters=300, tenure=(4, 9, 13), starts=starts)
     assert_same(g, o)
+
+
+def test_n_beyond_256_is_unsupported():
+    F = np.zeros((257, 257), dtype=np.int64)
+    with pytest.raises(q.QapError) as e:
+        q.qap_create(F, F)
+    assert e.value.status == q.EUNSUPPORTED
 
 
 def test_invalid_parameters_are_rejected():
