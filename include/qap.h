@@ -262,6 +262,62 @@ qap_status qap_batch_search_async(qap_batch* b, const qap_search_params* params,
                                   const qap_walk_outputs* out, int32_t p_stride, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Serving loop: continuous batching of solve requests (each request is a
+ * multi-walk search of its own instance, Sections 4.2 and 4.4).  A worker
+ * thread admits queued requests in arrival order as soon as a slot (a CUDA
+ * stream) is free and the device arena has room for the request's
+ * instance, outputs and workspace; admitted requests run on the device at
+ * the same time.  The arena is allocated once at creation, so serving does
+ * no cudaMalloc or cudaFree.  A request's results depend only on its own
+ * instance and parameters (walk ids 0..starts-1 of its seed), never on what
+ * else is running.
+ * ------------------------------------------------------------------------ */
+typedef struct qap_server qap_server;
+
+typedef struct {
+  int32_t slots;      /* requests on the device at once, 1..128             */
+  int32_t reserved;   /* must be 0                                          */
+  int64_t mem_bytes;  /* device arena for admitted requests, >= 1 MiB       */
+} qap_server_config;
+
+typedef struct {
+  double queued_us;   /* submit -> admission                                */
+  double device_us;   /* admission -> results on the host                   */
+  double total_us;    /* submit -> results on the host                      */
+} qap_request_times;
+
+typedef struct {
+  int64_t submitted, completed, pending, in_flight;
+  int64_t arena_bytes, arena_used;
+} qap_server_stats;
+
+/* Start a server on the current device.  Errors: QAP_EINVAL, QAP_ENOMEM,
+ * QAP_ECUDA. */
+qap_status qap_server_create(const qap_server_config* cfg, qap_server** out);
+
+/* Queue one request.  F, D (host, n x n int64) are copied before return;
+ * params->launch must be QAP_LAUNCH_PERSISTENT.  *ticket identifies the
+ * request for qap_server_wait.  Errors: as qap_create and qap_search, and
+ * QAP_ENOMEM when the request can never fit the arena. */
+qap_status qap_server_submit(qap_server* s, const int64_t* F, const int64_t* D, int32_t n,
+                             uint32_t flags, const qap_search_params* params,
+                             uint64_t* ticket);
+
+/* Wait at most timeout_ms for a request.  On completion its results are
+ * written to `out` (host pointers, rows as for qap_search, NULL fields
+ * skipped), its times to `times` (may be NULL), and the ticket is released.
+ * Returns QAP_ETIMEOUT (ticket kept) if it has not completed in time,
+ * QAP_EINVAL for an unknown ticket, or the request's own error. */
+qap_status qap_server_wait(qap_server* s, uint64_t ticket, int32_t timeout_ms,
+                           const qap_walk_outputs* out, qap_request_times* times);
+
+/* Counters of a server. */
+qap_status qap_server_get_stats(qap_server* s, qap_server_stats* out);
+
+/* Finish every queued and running request, then free the server. */
+void qap_server_destroy(qap_server* s);
+
+/* ------------------------------------------------------------------------
  * Batch search that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when
  * they search, for example a host runtime whose own allocator owns all

@@ -55,6 +55,21 @@ class WalkOutputs(ctypes.Structure):
                  "descent_moves", "hash", "descent_hash")]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mem_bytes", ctypes.c_int64)]
+
+
+class RequestTimes(ctypes.Structure):
+    _fields_ = [("queued_us", ctypes.c_double), ("device_us", ctypes.c_double),
+                ("total_us", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in
+                ("submitted", "completed", "pending", "in_flight", "arena_bytes", "arena_used")]
+
+
 class PlanInfo(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in
                 ("threads_per_walk", "pairs_per_thread", "smem_bytes", "grid", "ctas_per_sm",
@@ -120,6 +135,18 @@ def lib():
             L.qap_batch_search_noalloc.argtypes = [vp, ctypes.POINTER(SearchParams),
                                                    ctypes.POINTER(WalkOutputs), i32, vp]
             L.qap_batch_search_noalloc.restype = st
+            L.qap_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+            L.qap_server_create.restype = st
+            L.qap_server_submit.argtypes = [vp, vp, vp, i32, u32, ctypes.POINTER(SearchParams),
+                                            ctypes.POINTER(u64)]
+            L.qap_server_submit.restype = st
+            L.qap_server_wait.argtypes = [vp, u64, i32, ctypes.POINTER(WalkOutputs),
+                                          ctypes.POINTER(RequestTimes)]
+            L.qap_server_wait.restype = st
+            L.qap_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+            L.qap_server_get_stats.restype = st
+            L.qap_server_destroy.argtypes = [vp]
+            L.qap_server_destroy.restype = None
             _lib = L
     return _lib
 
@@ -405,3 +432,83 @@ class Batch:
             stream = torch.cuda.current_stream()
         qap_batch_search_async(self.h, params, {k: v.data_ptr() for k, v in outs.items()},
                                self.p_stride, stream.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# serving loop
+# ---------------------------------------------------------------------------
+
+def qap_server_create(slots=64, mem_bytes=1 << 30):
+    h = ctypes.c_void_p()
+    _check(lib().qap_server_create(ctypes.byref(ServerConfig(slots, 0, mem_bytes)),
+                                   ctypes.byref(h)), "qap_server_create")
+    return h
+
+
+def qap_server_submit(h, F, D, params, flags=0):
+    F = np.ascontiguousarray(F, dtype=np.int64)
+    D = np.ascontiguousarray(D, dtype=np.int64)
+    t = ctypes.c_uint64()
+    _check(lib().qap_server_submit(h, _ptr(F), _ptr(D), F.shape[0], flags, ctypes.byref(params),
+                                   ctypes.byref(t)), "qap_server_submit")
+    return t.value
+
+
+def qap_server_wait(h, ticket, n, walks, timeout_ms=60000):
+    """Results dict (numpy) and times dict of a finished request."""
+    out = {k: np.zeros((walks, n) if per_n else walks, dtype=dt)
+           for k, (dt, per_n) in OUTPUT_FIELDS.items()}
+    o = WalkOutputs(**{k: out[k].ctypes.data for k in OUTPUT_FIELDS})
+    tm = RequestTimes()
+    _check(lib().qap_server_wait(h, ticket, int(timeout_ms), ctypes.byref(o), ctypes.byref(tm)),
+           "qap_server_wait")
+    return out, {k: getattr(tm, k) for k, _ in RequestTimes._fields_}
+
+
+def qap_server_get_stats(h):
+    st = ServerStats()
+    _check(lib().qap_server_get_stats(h, ctypes.byref(st)), "qap_server_get_stats")
+    return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+
+def qap_server_destroy(h):
+    lib().qap_server_destroy(h)
+
+
+class Server:
+    """Owns one qap_server."""
+
+    def __init__(self, slots=64, mem_bytes=1 << 30):
+        self.h = qap_server_create(slots, mem_bytes)
+        self._shape = {}
+
+    def submit(self, F, D, params, force_int64=False):
+        t = qap_server_submit(self.h, F, D, params, FORCE_INT64 if force_int64 else 0)
+        self._shape[t] = (int(np.asarray(F).shape[0]), params.starts)
+        return t
+
+    def wait(self, ticket, timeout_ms=60000):
+        n, walks = self._shape[ticket]
+        res = qap_server_wait(self.h, ticket, n, walks, timeout_ms)
+        del self._shape[ticket]
+        return res
+
+    def stats(self):
+        return qap_server_get_stats(self.h)
+
+    def close(self):
+        if self.h is not None:
+            qap_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -19,10 +19,11 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libqap.so")
 
 UNITS = ["qap_api.cu", "qap_walk_i32_f8.cu", "qap_walk_i32_f16.cu", "qap_walk_i64_f16.cu",
-         "qap_batch_i32_f8.cu", "qap_batch_i32_f16.cu", "qap_batch_i64_f16.cu"]
+         "qap_batch_i32_f8.cu", "qap_batch_i32_f16.cu", "qap_batch_i64_f16.cu",
+         "qap_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "-I", INCLUDE]
+         "-Xcompiler", "-pthread", "-I", INCLUDE]
 
 
 def _nvcc():
@@ -37,7 +38,7 @@ def _digest():
     h.update(" ".join(ARCH + FLAGS).encode())
     for d in (CSRC, INCLUDE):
         for name in sorted(os.listdir(d)):
-            if name.endswith((".cu", ".cuh", ".h")):
+            if name.endswith((".cu", ".cuh", ".h", ".py")) and name != "__init__.py":
                 with open(os.path.join(d, name), "rb") as f:
                     h.update(name.encode())
                     h.update(f.read())
@@ -68,7 +69,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         logs = list(ex.map(compile_one, UNITS, objs))
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
+    subprocess.run([nvcc, *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs],
+                   check=True)
     os.replace(tmp, LIB)
     with open(stamp, "w") as f:
         f.write(digest)

@@ -1,0 +1,360 @@
+// Host-side helpers shared by the C-ABI entry points (qap_api.cu) and the
+// serving loop (qap_server.cu): instance inspection and upload images, launch
+// planning, argument marshalling and output buffers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "../../include/qap.h"
+#include "qap_kernels.cuh"
+
+namespace qapk {
+WalkKernelFn walk_kernel_i32_f8(int nt, int maxpt, int store);
+WalkKernelFn walk_kernel_i32_f16(int nt, int maxpt, int store);
+WalkKernelFn walk_kernel_i64_f16(int nt, int maxpt, int store);
+BatchKernelFn batch_kernel_i32_f8(int nt, int maxpt, int store);
+BatchKernelFn batch_kernel_i32_f16(int nt, int maxpt, int store);
+BatchKernelFn batch_kernel_i64_f16(int nt, int maxpt, int store);
+}  // namespace qapk
+
+namespace qaph {
+
+// Detail of the last QAP_ECUDA (per host thread).
+extern thread_local char g_last_error[256];
+
+inline qap_status cuda_fail(cudaError_t e, const char* where) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+  return QAP_ECUDA;
+}
+
+#define QAP_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+#define QAP_TRY(call)                  \
+  do {                                 \
+    qap_status s_ = (call);            \
+    if (s_ != QAP_OK) return s_;       \
+  } while (0)
+
+// Largest n: keys pack (r << 8 | s) into 16 bits.
+inline constexpr int kMaxN = 256;
+
+struct Plan {
+  int nt;
+  int maxpt;
+  int store;  // 0, or qapk::kGlobalDelta [| qapk::kGlobalFlow] (large-n plans)
+};
+
+// The large-n plan: 1024 threads, up to 40 slots each in a global workspace
+// (row_segments(256, 40) = 945).
+inline constexpr Plan kLargePlan = {1024, 40, qapk::kGlobalDelta};
+
+// Register plans (threads per walk, pair slots per thread) compiled into the
+// library.  A plan fits n when its row segments (qapk::row_segments) number
+// at most its threads.  The automatic choice takes the fewest threads that fit
+// with at most eight slots, else the fewest threads that fit at all; for a
+// given thread count the fewest slots that fit.
+inline constexpr Plan kPlans[] = {{128, 4, 0},   {128, 12, 0},  {256, 6, 0},   {256, 8, 0},
+                       {512, 4, 0},   {512, 8, 0},   {512, 12, 0},  {1024, 8, 0},
+                       {1024, 12, 0}, {1024, 16, 0}, {1024, 20, 0}};
+
+inline bool plan_for(int n, int nt, Plan* out) {
+  for (const Plan& p : kPlans)
+    if (p.nt == nt && qapk::row_segments(n, p.maxpt) <= nt) {
+      *out = p;
+      return true;
+    }
+  return false;
+}
+
+inline bool choose_plan(int n, int threads, Plan* out) {
+  if (threads != 0) return plan_for(n, threads, out);
+  for (int pass = 0; pass < 2; ++pass)
+    for (int nt : {128, 256, 512, 1024}) {
+      Plan p;
+      if (plan_for(n, nt, &p) && (pass == 1 || p.maxpt <= 8)) {
+        *out = p;
+        return true;
+      }
+    }
+  return false;
+}
+
+// Widest power-of-two group (<= 8 lanes, <= the row chunks) that still gives
+// every index of phase X its own group.
+inline int group_for(int n, int nt, int fbytes) {
+  const int w = 16 / fbytes;
+  const int nc = (n + w - 1) / w;
+  int g = 8;
+  while (g > 1 && (nt / g < n || g > nc)) g >>= 1;
+  return g;
+}
+
+// One instance's shape on the device: F, F^T in `fbytes` elements with rows
+// of an odd number of 16-byte chunks (rows read side by side by the lanes of
+// a warp then fall in different banks), D as int8.
+struct DevInstance {
+  int n = 0, ldF = 0, ldP = 0, symF = 0, symD = 0;
+  int64_t bound = 0;
+  int64_t maxF = 0;
+};
+
+inline int pad_ldF(int n, int fbytes) { return (16 / fbytes) * (((n * fbytes + 15) / 16) | 1); }
+inline int pad_ldP(int n) { return 16 * (((n + 15) / 16) | 1); }
+
+// Checks ranges and symmetry of one instance.
+inline qap_status inspect_instance(const int64_t* F, const int64_t* D, int n, DevInstance* di) {
+  if (!F || !D || n < 2) return QAP_EINVAL;
+  if (n > kMaxN) return QAP_EUNSUPPORTED;
+  int64_t mF = 0, mD = 0;
+  int symF = 1, symD = 1;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const int64_t f = F[(size_t)i * n + j], d = D[(size_t)i * n + j];
+      if (f < INT16_MIN || f > INT16_MAX || d < INT8_MIN || d > INT8_MAX) return QAP_EUNSUPPORTED;
+      mF = std::max<int64_t>(mF, f < 0 ? -f : f);
+      mD = std::max<int64_t>(mD, d < 0 ? -d : d);
+      if (f != F[(size_t)j * n + i]) symF = 0;
+      if (d != D[(size_t)j * n + i]) symD = 0;
+    }
+  const int64_t nn = n;
+  di->n = n;
+  di->symF = symF;
+  di->symD = symD;
+  di->bound = (nn * nn + 8 * nn + 32) * mF * mD;  // < 2^40 for n <= 181
+  di->maxF = mF;
+  return QAP_OK;
+}
+
+// Host images of F, F^T and D for the chosen element width.
+inline void build_images(const int64_t* F, const int64_t* D, const DevInstance& di, int fbytes,
+                  std::vector<unsigned char>& img_F, std::vector<unsigned char>& img_Ft,
+                  std::vector<unsigned char>& img_D) {
+  const int n = di.n, ld = di.ldF;
+  img_F.assign((size_t)n * ld * fbytes, 0);
+  img_Ft.assign((size_t)n * ld * fbytes, 0);
+  img_D.resize((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const int64_t f = F[(size_t)i * n + j];
+      if (fbytes == 1) {
+        reinterpret_cast<int8_t*>(img_F.data())[(size_t)i * ld + j] = (int8_t)f;
+        reinterpret_cast<int8_t*>(img_Ft.data())[(size_t)j * ld + i] = (int8_t)f;
+      } else {
+        reinterpret_cast<int16_t*>(img_F.data())[(size_t)i * ld + j] = (int16_t)f;
+        reinterpret_cast<int16_t*>(img_Ft.data())[(size_t)j * ld + i] = (int16_t)f;
+      }
+      img_D[(size_t)i * n + j] = (unsigned char)(int8_t)D[(size_t)i * n + j];
+    }
+}
+
+inline qap_status device_attrs(int* device, int* sms, int* smem_optin) {
+  QAP_CUDA(cudaGetDevice(device));
+  QAP_CUDA(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, *device));
+  QAP_CUDA(cudaDeviceGetAttribute(smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, *device));
+  return QAP_OK;
+}
+
+inline qapk::WalkKernelFn pick_walk_kernel(int dbytes, int fbytes, const Plan& p) {
+  if (dbytes == 8) return qapk::walk_kernel_i64_f16(p.nt, p.maxpt, p.store);
+  if (fbytes == 1) return qapk::walk_kernel_i32_f8(p.nt, p.maxpt, p.store);
+  return qapk::walk_kernel_i32_f16(p.nt, p.maxpt, p.store);
+}
+
+inline qapk::BatchKernelFn pick_batch_kernel(int dbytes, int fbytes, const Plan& p) {
+  if (dbytes == 8) return qapk::batch_kernel_i64_f16(p.nt, p.maxpt, p.store);
+  if (fbytes == 1) return qapk::batch_kernel_i32_f8(p.nt, p.maxpt, p.store);
+  return qapk::batch_kernel_i32_f16(p.nt, p.maxpt, p.store);
+}
+
+// Shared memory of a plan for the instance shapes `d` (the largest over them).
+inline int plan_smem(const Plan& p, const DevInstance* d, int count, int fbytes, int dbytes) {
+  int smem = 0;
+  for (int i = 0; i < count; ++i)
+    smem = std::max(smem, qapk::smem_layout(d[i].n, d[i].ldF, fbytes, d[i].ldP, d[i].symF,
+                                            d[i].symD, dbytes, p.nt * p.maxpt, p.store)
+                              .bytes);
+  return smem;
+}
+
+// A register plan when one holds n and fits shared memory; else the large-n
+// plan, with F in global memory when it does not fit shared memory either.
+inline bool choose_plan_fit(int nmax, int threads, const DevInstance* d, int count, int fbytes,
+                     int dbytes, int smem_optin, int reserve, Plan* out) {
+  Plan p;
+  if (nmax <= 181 && choose_plan(nmax, threads, &p) &&
+      plan_smem(p, d, count, fbytes, dbytes) + reserve <= smem_optin) {
+    *out = p;
+    return true;
+  }
+  if (threads != 0 && threads != kLargePlan.nt) return false;
+  if (qapk::row_segments(nmax, kLargePlan.maxpt) > kLargePlan.nt) return false;
+  p = kLargePlan;
+  if (plan_smem(p, d, count, fbytes, dbytes) + reserve > smem_optin)
+    p.store |= qapk::kGlobalFlow;
+  if (plan_smem(p, d, count, fbytes, dbytes) + reserve > smem_optin) return false;
+  *out = p;
+  return true;
+}
+
+inline size_t workspace_per_cta(const Plan& p, int dbytes) {
+  if (!(p.store & qapk::kGlobalDelta)) return 0;
+  const size_t b = (size_t)p.nt * p.maxpt * ((size_t)dbytes + 4);
+  return (b + 255) / 256 * 256;
+}
+
+extern std::mutex g_attr_mu;
+
+inline qap_status prepare_kernel(const void* fn, int smem) {
+  // cudaFuncSetAttribute is idempotent; serialise to keep it cheap and safe.
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  QAP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  return QAP_OK;
+}
+
+inline qap_status validate_params(const qap_search_params* p) {
+  if (!p) return QAP_EINVAL;
+  if (p->starts < 1 || p->iters < 0) return QAP_EINVAL;
+  if (p->descend != 0 && p->descend != 1) return QAP_EINVAL;
+  if (p->aspiration != 0 && p->aspiration != 1) return QAP_EINVAL;
+  if (p->iters > 0) {
+    if (p->tenure.tmin < 1 || p->tenure.tmax < p->tenure.tmin || p->tenure.period < 0)
+      return QAP_EINVAL;
+    // tabu_until = it + t must stay below INT_MAX
+    if ((int64_t)p->iters + (int64_t)p->tenure.tmax >= (int64_t)INT_MAX) return QAP_EINVAL;
+  }
+  if (p->launch != QAP_LAUNCH_PERSISTENT && p->launch != QAP_LAUNCH_PLAIN) return QAP_EINVAL;
+  if (p->tenure_per_n != 0 && p->tenure_per_n != 1) return QAP_EINVAL;
+  if (p->tenure_per_n && p->iters > 0 &&
+      ((int64_t)p->tenure.tmax * kMaxN / 10 + 1 + p->iters >= (int64_t)INT_MAX ||
+       (int64_t)p->tenure.period * kMaxN > (int64_t)INT_MAX))
+    return QAP_EINVAL;
+  const int t = p->threads_per_walk;
+  if (t != 0 && t != 128 && t != 256 && t != 512 && t != 1024) return QAP_EINVAL;
+  return QAP_OK;
+}
+
+inline qapk::SearchArgs make_search_args(const qap_search_params* p, const qap_walk_outputs* o,
+                                  int p_stride) {
+  qapk::SearchArgs a{};
+  a.walk_base = p->walk_base;
+  a.seed = p->seed;
+  a.descend = p->descend;
+  a.max_descent = p->max_descent;
+  a.iters = p->iters;
+  a.tmin = p->tenure.tmin;
+  a.tmax = p->tenure.tmax;
+  a.period = p->tenure.period;
+  a.aspiration = p->aspiration;
+  a.tenure_per_n = p->tenure_per_n;
+  a.p_stride = p_stride;
+  a.best_p = o->best_p;
+  a.best_cost = o->best_cost;
+  a.final_cost = o->final_cost;
+  a.best_iter = o->best_iter;
+  a.iters_done = o->iters_done;
+  a.status = o->status;
+  a.descent_moves = o->descent_moves;
+  a.hash = o->hash;
+  a.descent_hash = o->descent_hash;
+  return a;
+}
+
+inline bool is_permutation(const int32_t* p, int n, std::vector<char>& seen) {
+  seen.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (p[i] < 0 || p[i] >= n || seen[p[i]]) return false;
+    seen[p[i]] = 1;
+  }
+  return true;
+}
+
+inline qap_status grow(void** buf, size_t* have, size_t bytes) {
+  if (bytes <= *have) return QAP_OK;
+  if (*buf) {
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+  }
+  cudaError_t e = cudaMalloc(buf, bytes);
+  if (e == cudaErrorMemoryAllocation) return QAP_ENOMEM;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  *have = bytes;
+  return QAP_OK;
+}
+
+// Device outputs of W walks carved from one buffer; rows of best_p hold
+// p_stride elements.
+struct OutLayout {
+  size_t off_p, off_i64, off_i32, total;
+};
+
+inline OutLayout out_layout(int W, int p_stride) {
+  OutLayout L;
+  const size_t perm = (size_t)W * p_stride * sizeof(int32_t);
+  L.off_p = 0;
+  L.off_i64 = (perm + 255) / 256 * 256;
+  L.off_i32 = L.off_i64 + (size_t)4 * W * 8;
+  L.total = L.off_i32 + (size_t)4 * W * 4 + 256;
+  return L;
+}
+
+inline qap_walk_outputs carve_outputs(char* base, const OutLayout& L, int W) {
+  qap_walk_outputs d{};
+  d.best_p = reinterpret_cast<int32_t*>(base + L.off_p);
+  int64_t* i64 = reinterpret_cast<int64_t*>(base + L.off_i64);
+  int32_t* i32 = reinterpret_cast<int32_t*>(base + L.off_i32);
+  d.best_cost = i64;
+  d.final_cost = i64 + W;
+  d.hash = reinterpret_cast<uint64_t*>(i64 + 2 * W);
+  d.descent_hash = reinterpret_cast<uint64_t*>(i64 + 3 * W);
+  d.best_iter = i32;
+  d.iters_done = i32 + W;
+  d.status = i32 + 2 * W;
+  d.descent_moves = i32 + 3 * W;
+  return d;
+}
+
+inline qap_status copy_outputs_back(const qap_walk_outputs* out, const qap_walk_outputs& d, int W,
+                             int p_stride, cudaStream_t s) {
+  auto d2h = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) : cudaSuccess;
+  };
+  QAP_CUDA(d2h(out->best_p, d.best_p, (size_t)W * p_stride * 4));
+  QAP_CUDA(d2h(out->best_cost, d.best_cost, (size_t)W * 8));
+  QAP_CUDA(d2h(out->final_cost, d.final_cost, (size_t)W * 8));
+  QAP_CUDA(d2h(out->hash, d.hash, (size_t)W * 8));
+  QAP_CUDA(d2h(out->descent_hash, d.descent_hash, (size_t)W * 8));
+  QAP_CUDA(d2h(out->best_iter, d.best_iter, (size_t)W * 4));
+  QAP_CUDA(d2h(out->iters_done, d.iters_done, (size_t)W * 4));
+  QAP_CUDA(d2h(out->status, d.status, (size_t)W * 4));
+  QAP_CUDA(d2h(out->descent_moves, d.descent_moves, (size_t)W * 4));
+  QAP_CUDA(cudaStreamSynchronize(s));
+  return QAP_OK;
+}
+
+inline qapk::InstArgs inst_args(const DevInstance& d, const void* F, const void* Ft, const int8_t* D,
+                         int nt, int fbytes) {
+  qapk::InstArgs I{};
+  I.n = d.n;
+  I.ldF = d.ldF;
+  I.ldP = d.ldP;
+  I.symF = d.symF;
+  I.symD = d.symD;
+  I.group = group_for(d.n, nt, fbytes);
+  I.F = F;
+  I.Ft = d.symF ? F : Ft;
+  I.D = D;
+  return I;
+}
+
+}  // namespace qaph
