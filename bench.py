@@ -212,8 +212,15 @@ def main():
     ap.add_argument("--iters", type=int, default=0,
                     help="override the iteration count (smaller cases for profiling)")
     ap.add_argument("--walks", type=int, default=0, help="override the walk count")
+    ap.add_argument("--workload", choices=["asym50", "grid100", "batch512", "serve"],
+                    default="asym50",
+                    help="asym50 is the benchmark line; the others measure the remaining "
+                         "workloads (one JSON line each)")
+    ap.add_argument("--requests", type=int, default=600, help="serve: requests per run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload != "asym50" and args.impl == "ours":
+        return other_workloads(args)
 
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -366,6 +373,151 @@ def main():
     inst.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def timed_steps(step, steps, stream, flush, dev):
+    """Device time of `steps` calls of step(), L2 flushed between them."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    gpu_uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    gpu_id = gpu_uuid if gpu_uuid.startswith("GPU-") else f"GPU-{gpu_uuid}"
+    torch.cuda.synchronize(dev)
+    with ClockSampler(gpu_id) as clocks:
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.fill_(k & 0xff)
+                ev[k][0].record(stream)
+                step()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+    return [a.elapsed_time(b) for a, b in ev], clocks.summary()
+
+
+def other_workloads(args):
+    """The remaining workloads, one JSON line each (N = 1)."""
+    import torch
+    import paper_2307_11248_gb300 as q
+    from paper_2307_11248_gb300 import instances
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    line = {"unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic"}
+
+    if args.workload == "grid100":
+        w = instances.workload_grid100()
+        n = w["F"].shape[0]
+        T = n * (n - 1) // 2
+        W = args.walks or w["walks"]
+        iters = args.iters or w["iters"]
+        inst = q.Instance(w["F"], w["D"])
+        prm = q.make_params(W, seed=w["seed"], iters=iters, tenure=w["tenure"], descend=True)
+        outs = inst.device_outputs(W, device=dev)
+        with torch.cuda.stream(stream):
+            inst.search_async(prm, outs, stream=stream)
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()  # the whole search as one graph launch
+        with torch.cuda.graph(graph, stream=stream):
+            inst.search_async(prm, outs, stream=stream)
+        for _ in range(args.warmup):
+            graph.replay()
+        ms, clk = timed_steps(graph.replay, args.steps, stream, flush, dev)
+        moves = float(outs["iters_done"].sum().item() + outs["descent_moves"].sum().item())
+        plan = inst.plan(prm)
+        line.update(metric=METRIC, value=moves * T / (sum(ms) / 1e3 / args.steps),
+                    ms_per_step=sum(ms) / args.steps, steps=args.steps, warmup=args.warmup,
+                    dtype="int32" if inst.info["delta_bytes"] == 4 else "int64",
+                    tabu_iters_per_s=float(outs["iters_done"].sum().item()) /
+                    (sum(ms) / 1e3 / args.steps),
+                    config={"workload": f"2opt then tabu, n=100 grid, {W} walks x {iters} iters",
+                            "launch": "persistent, replayed as one CUDA graph",
+                            "threads_per_walk": plan["threads_per_walk"], "grid": plan["grid"],
+                            "evals": "2opt moves and tabu iterations, n(n-1)/2 each",
+                            "l2": "flushed between timed steps"},
+                    gpu_launches=args.steps, clocks=clk)
+    elif args.workload == "batch512":
+        w = instances.workload_batch512()
+        insts = w["instances"]
+        W = args.walks or w["walks"]
+        iters = args.iters or w["iters"]
+        b = q.Batch([i.F for i in insts], [i.D for i in insts], force_int64=True)
+        prm = q.make_params(W, seed=w["seed"], iters=iters, tenure=(9, 11, 20), tenure_per_n=True)
+        outs = b.device_outputs(W, device=dev)
+        step = lambda: b.search_async(prm, outs, stream=stream)  # noqa: E731
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+        ms, clk = timed_steps(step, args.steps, stream, flush, dev)
+        it = outs["iters_done"].cpu().numpy().reshape(len(insts), W)
+        evals = sum(float(it[i].sum()) * insts[i].n * (insts[i].n - 1) / 2
+                    for i in range(len(insts)))
+        plan = b.plan(prm)
+        line.update(metric=METRIC, value=evals / (sum(ms) / 1e3 / args.steps),
+                    ms_per_step=sum(ms) / args.steps, steps=args.steps, warmup=args.warmup,
+                    dtype="int64", tabu_iters_per_s=float(it.sum()) / (sum(ms) / 1e3 / args.steps),
+                    config={"workload": f"{len(insts)} lognormal instances, n in [20,150], "
+                                        f"{W} walks x {iters} iters each",
+                            "launch": "one persistent launch, device work queue, largest n first",
+                            "threads_per_walk": plan["threads_per_walk"],
+                            "pairs_per_thread": plan["pairs_per_thread"], "grid": plan["grid"],
+                            "l2": "flushed between timed steps"},
+                    gpu_launches=args.steps, clocks=clk)
+    else:
+        line.update(serve(args, q, instances))
+    print(json.dumps(line))
+
+
+def serve(args, q, instances):
+    """Poisson stream of 32-walk x 2000-iteration tabu requests, n in
+    [12, 256], through the serving loop: solves/s and latency percentiles,
+    at the offered 2000 req/s and at 0.8x the measured capacity."""
+    count = args.requests
+    reqs = instances.poisson_requests(count, seed=4, rate_per_s=2000.0)
+    prms = [q.make_params(32, seed=r.rid, iters=2000, tenure=instances.baseline_tenure(r.inst.n))
+            for r in reqs]
+    warm = instances.poisson_requests(20, seed=99)
+
+    def run(rate, sv):
+        t0 = time.perf_counter()
+        tickets = []
+        for r, p in zip(reqs, prms):
+            due = t0 + (r.arrival_s * 2000.0 / rate if rate else 0.0)
+            now = time.perf_counter()
+            if due > now:
+                time.sleep(due - now)
+            tickets.append(sv.submit(r.inst.F, r.inst.D, p))
+        lat = []
+        for t in tickets:
+            _, tm = sv.wait(t, timeout_ms=600000)
+            lat.append(tm["total_us"] / 1e3)
+        wall = time.perf_counter() - t0
+        lat = np.array(lat)
+        return {"solves_per_s": count / wall, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall}
+
+    with q.Server(slots=64, mem_bytes=2 << 30) as sv:
+        for r in warm:
+            sv.wait(sv.submit(r.inst.F, r.inst.D, q.make_params(
+                32, seed=r.rid, iters=200, tenure=instances.baseline_tenure(r.inst.n))))
+        saturated = run(0, sv)            # all at once: capacity
+        offered = run(2000.0, sv)         # the offered Poisson rate
+        rate80 = 0.8 * saturated["solves_per_s"]
+        at80 = run(rate80, sv)
+    evals = sum(32 * 2000 * r.inst.n * (r.inst.n - 1) / 2 for r in reqs)
+    return {"metric": "solves/s (serving, 32-walk x 2000-iteration tabu requests)",
+            "value": offered["solves_per_s"], "unit": "solves/s", "steps": 1, "warmup": 1,
+            "ms_per_step": offered["wall_s"] * 1e3, "dtype": "int32",
+            "p50_ms": offered["p50_ms"], "p99_ms": offered["p99_ms"],
+            "overloaded": offered["solves_per_s"] < 0.95 * 2000.0,
+            "capacity_solves_per_s": saturated["solves_per_s"],
+            "at_0.8_capacity": {"rate": rate80, **at80},
+            "swap_evals_per_s_at_capacity": evals / saturated["wall_s"],
+            "config": {"workload": f"{count} Poisson requests (2000/s offered), n in [12,256], "
+                                   "generators sym uniform / asym uniform / grid",
+                       "server": "64 slots, 2 GiB arena, FIFO admission by slot and memory"},
+            "gpu_launches": 3 * count}
 
 
 if __name__ == "__main__":

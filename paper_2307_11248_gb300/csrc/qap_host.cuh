@@ -215,9 +215,19 @@ inline size_t workspace_per_cta(const Plan& p, int dbytes) {
 extern std::mutex g_attr_mu;
 
 inline qap_status prepare_kernel(const void* fn, int smem) {
-  // cudaFuncSetAttribute is idempotent; serialise to keep it cheap and safe.
+  // The dynamic shared-memory limit is a property of the function, shared
+  // by every launch of it from any thread; raise it once to the device
+  // maximum so that no launch can find it lowered by a smaller request.
+  static std::vector<const void*> done;
   std::lock_guard<std::mutex> lk(g_attr_mu);
-  QAP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  for (const void* f : done)
+    if (f == fn) return QAP_OK;
+  int dev = 0, optin = 0;
+  QAP_CUDA(cudaGetDevice(&dev));
+  QAP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > optin) return QAP_EUNSUPPORTED;
+  QAP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  done.push_back(fn);
   return QAP_OK;
 }
 

@@ -93,6 +93,7 @@ struct Request {
   std::vector<unsigned char> out;  // the device output block
   Clock::time_point t_submit, t_admit, t_done;
   qap_status result = QAP_OK;
+  char err[256] = "";  // CUDA error text recorded by the worker thread
   bool done = false;
 };
 
@@ -218,6 +219,7 @@ void finish(qap_server* sv, int slot_idx, qap_status st) {
     const OutLayout OL = out_layout(r->params.starts, r->di.n);
     r->out.assign(sl.pinned, sl.pinned + OL.total);
   }
+  if (st == QAP_ECUDA) snprintf(r->err, sizeof(r->err), "%s", g_last_error);
   std::lock_guard<std::mutex> lk(sv->mu);
   sv->arena.release(r->off, r->bytes);
   r->iF.clear();
@@ -355,6 +357,7 @@ qap_status qap_server_wait(qap_server* sv, uint64_t ticket, int32_t timeout_ms,
   if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; }))
     return QAP_ETIMEOUT;
   const qap_status st = r->result;
+  if (st == QAP_ECUDA) snprintf(g_last_error, sizeof(g_last_error), "%s", r->err);
   if (st == QAP_OK && out) {
     const int W = r->params.starts, n = r->di.n;
     const OutLayout OL = out_layout(W, n);
