@@ -443,7 +443,7 @@ def other_workloads(args):
         W = args.walks or w["walks"]
         iters = args.iters or w["iters"]
         b = q.Batch([i.F for i in insts], [i.D for i in insts], force_int64=True)
-        prm = q.make_params(W, seed=w["seed"], iters=iters, tenure=(9, 11, 20), tenure_per_n=True)
+        prm = q.make_params(W, seed=w["seed"], iters=iters, tenure=(90, 110, 200), tenure_per_n=True)
         outs = b.device_outputs(W, device=dev)
         step = lambda: b.search_async(prm, outs, stream=stream)  # noqa: E731
         with torch.cuda.stream(stream):

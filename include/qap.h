@@ -139,11 +139,13 @@ typedef struct {
   int32_t launch;          /* QAP_LAUNCH_PERSISTENT or QAP_LAUNCH_PLAIN      */
   int32_t threads_per_walk;/* 0 = automatic; else 128, 256, 512 or 1024
                               (n > 181 always uses 1024)                     */
-  int32_t tenure_per_n;    /* 1: tenure.tmin, tmax, period are tenths of each
-                              instance's n: tmin' = max(1, floor(tmin n / 10)),
-                              tmax' = max(tmin', ceil(tmax n / 10)),
-                              period' = period n / 10 (integer division);
-                              0: absolute                                    */
+  int32_t tenure_per_n;    /* 1: tenure.tmin, tmax, period are hundredths of
+                              each instance's n:
+                              tmin' = max(1, floor(tmin n / 100)),
+                              tmax' = max(tmin', ceil(tmax n / 100)),
+                              period' = floor(period n / 100);
+                              e.g. (10, 33, 0) is the paper's [0.1n, 0.33n]
+                              drawn per move; 0: absolute                    */
 } qap_search_params;
 
 /* Per-walk outputs; every pointer may be NULL except best_cost.  For
@@ -157,7 +159,12 @@ typedef struct {
  *   status        W      0 = completed, 1 = stopped early: no admissible move
  *   descent_moves W      moves applied by the 2opt phase
  *   hash          W      trajectory hash of the tabu phase
- *   descent_hash  W      trajectory hash of the 2opt phase */
+ *   descent_hash  W      trajectory hash of the 2opt phase
+ *   freq          W x m x m  the frequency memory of Section 4.3: entry
+ *                        [s][r] (r < s, lower triangle) counts how often the
+ *                        tabu phase applied move (r, s); every other entry
+ *                        is 0.  m = n for one instance, p_stride for a batch.
+ *                        Not produced by the serving loop. */
 typedef struct {
   int32_t* best_p;
   int64_t* best_cost;
@@ -168,6 +175,7 @@ typedef struct {
   int32_t* descent_moves;
   uint64_t* hash;
   uint64_t* descent_hash;
+  int32_t* freq;
 } qap_walk_outputs;
 
 /* Run W independent walks of one instance; host buffers, blocking.

@@ -52,7 +52,7 @@ class SearchParams(ctypes.Structure):
 class WalkOutputs(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in
                 ("best_p", "best_cost", "final_cost", "best_iter", "iters_done", "status",
-                 "descent_moves", "hash", "descent_hash")]
+                 "descent_moves", "hash", "descent_hash", "freq")]
 
 
 class ServerConfig(ctypes.Structure):
@@ -171,8 +171,9 @@ def _ptr(a):
 def make_params(starts, *, seed=0, iters=0, tenure=(1, 1, 0), aspiration=True, descend=False,
                 max_descent=-1, walk_base=0, launch=LAUNCH_PERSISTENT, threads_per_walk=0,
                 tenure_per_n=False):
-    """Search parameters.  With tenure_per_n, `tenure` is given in tenths of
-    each instance's n (e.g. (9, 11, 20) is [0.9n, 1.1n] redrawn every 2n)."""
+    """Search parameters.  With tenure_per_n, `tenure` is given in hundredths
+    of each instance's n (e.g. (90, 110, 200) is [0.9n, 1.1n] redrawn every
+    2n; (10, 33, 0) is the paper's [0.1n, 0.33n] drawn per move)."""
     return SearchParams(int(starts), int(walk_base), int(bool(descend)), int(max_descent),
                         int(iters), Tenure(*[int(t) for t in tenure]), int(bool(aspiration)),
                         int(seed) & (2**64 - 1), int(launch), int(threads_per_walk),
@@ -219,8 +220,9 @@ def qap_plan(h, params):
     return {k: getattr(info, k) for k, _ in PlanInfo._fields_}
 
 
-def qap_search(h, params, starts=None, n=None):
-    """Blocking search with host buffers; returns a dict of numpy arrays."""
+def qap_search(h, params, starts=None, n=None, freq=False):
+    """Blocking search with host buffers; returns a dict of numpy arrays
+    (with ``freq``, also the W x n x n frequency memory)."""
     if n is None:
         n = qap_info(h)["n"]
     W = params.starts
@@ -231,7 +233,11 @@ def qap_search(h, params, starts=None, n=None):
             raise ValueError("starts must be W x n")
     out = {k: np.zeros((W, n) if per_n else W, dtype=dt)
            for k, (dt, per_n) in OUTPUT_FIELDS.items()}
-    o = WalkOutputs(**{k: out[k].ctypes.data for k in OUTPUT_FIELDS})
+    ptrs = {k: out[k].ctypes.data for k in OUTPUT_FIELDS}
+    if freq:
+        out["freq"] = np.zeros((W, n, n), dtype=np.int32)
+        ptrs["freq"] = out["freq"].ctypes.data
+    o = WalkOutputs(**ptrs)
     _check(lib().qap_search(h, ctypes.byref(params), _ptr(st), ctypes.byref(o)), "qap_search")
     return out
 
@@ -241,7 +247,7 @@ def qap_search_async(h, params, d_starts, d_out, stream):
 
     d_starts: device pointer (int) or 0; d_out: dict name -> device pointer
     (int; missing names are NULL); stream: cudaStream_t as an int."""
-    o = WalkOutputs(**{k: int(d_out.get(k, 0) or 0) for k in OUTPUT_FIELDS})
+    o = WalkOutputs(**{k: int(d_out.get(k, 0) or 0) for k in list(OUTPUT_FIELDS) + ["freq"]})
     _check(lib().qap_search_async(h, ctypes.byref(params), ctypes.c_void_p(int(d_starts or 0)),
                                   ctypes.byref(o), ctypes.c_void_p(int(stream or 0))),
            "qap_search_async")
@@ -306,8 +312,8 @@ class Instance:
     def plan(self, params):
         return qap_plan(self.h, params)
 
-    def search(self, params, starts=None):
-        return qap_search(self.h, params, starts, n=self.n)
+    def search(self, params, starts=None, freq=False):
+        return qap_search(self.h, params, starts, n=self.n, freq=freq)
 
     def device_outputs(self, walks, device="cuda"):
         """torch tensors for every output of a search of `walks` walks."""
@@ -360,19 +366,24 @@ def qap_batch_plan(h, params):
     return {k: getattr(info, k) for k, _ in PlanInfo._fields_}
 
 
-def qap_batch_search(h, params, p_stride):
-    """Blocking batch search; rows i * starts + k; best_p rows of p_stride."""
+def qap_batch_search(h, params, p_stride, freq=False):
+    """Blocking batch search; rows i * starts + k; best_p rows of p_stride
+    (with ``freq``, also W x p_stride x p_stride frequency memories)."""
     W = qap_batch_info(h)["count"] * params.starts
     out = {k: np.zeros((W, p_stride) if per_n else W, dtype=dt)
            for k, (dt, per_n) in OUTPUT_FIELDS.items()}
-    o = WalkOutputs(**{k: out[k].ctypes.data for k in OUTPUT_FIELDS})
+    ptrs = {k: out[k].ctypes.data for k in OUTPUT_FIELDS}
+    if freq:
+        out["freq"] = np.zeros((W, p_stride, p_stride), dtype=np.int32)
+        ptrs["freq"] = out["freq"].ctypes.data
+    o = WalkOutputs(**ptrs)
     _check(lib().qap_batch_search(h, ctypes.byref(params), ctypes.byref(o), p_stride),
            "qap_batch_search")
     return out
 
 
 def qap_batch_search_async(h, params, d_out, p_stride, stream):
-    o = WalkOutputs(**{k: int(d_out.get(k, 0) or 0) for k in OUTPUT_FIELDS})
+    o = WalkOutputs(**{k: int(d_out.get(k, 0) or 0) for k in list(OUTPUT_FIELDS) + ["freq"]})
     _check(lib().qap_batch_search_async(h, ctypes.byref(params), ctypes.byref(o), p_stride,
                                         ctypes.c_void_p(int(stream or 0))),
            "qap_batch_search_async")
@@ -416,8 +427,8 @@ class Batch:
     def plan(self, params):
         return qap_batch_plan(self.h, params)
 
-    def search(self, params):
-        return qap_batch_search(self.h, params, self.p_stride)
+    def search(self, params, freq=False):
+        return qap_batch_search(self.h, params, self.p_stride, freq=freq)
 
     def device_outputs(self, walks, device="cuda"):
         import torch

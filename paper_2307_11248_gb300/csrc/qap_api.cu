@@ -290,9 +290,12 @@ qap_status qap_search(qap_ctx* ctx, const qap_search_params* params, const int32
   QAP_CUDA(cudaSetDevice(ctx->device));
   const OutLayout L = out_layout(W, n);
   const size_t starts_off = (L.total + 255) / 256 * 256;
-  QAP_TRY(grow(&ctx->scratch, &ctx->scratch_bytes, starts_off + (size_t)W * n * 4));
+  const size_t freq_off = starts_off + ((size_t)W * n * 4 + 255) / 256 * 256;
+  const size_t freq_bytes = out->freq ? (size_t)W * n * n * 4 : 0;
+  QAP_TRY(grow(&ctx->scratch, &ctx->scratch_bytes, freq_off + freq_bytes));
   char* base = static_cast<char*>(ctx->scratch);
-  const qap_walk_outputs d = carve_outputs(base, L, W);
+  qap_walk_outputs d = carve_outputs(base, L, W);
+  if (out->freq) d.freq = reinterpret_cast<int32_t*>(base + freq_off);
   int32_t* d_starts = reinterpret_cast<int32_t*>(base + starts_off);
   cudaStream_t s = ctx->stream;
   if (starts)
@@ -505,8 +508,11 @@ qap_status qap_batch_search(qap_batch* b, const qap_search_params* params,
   QAP_CUDA(cudaSetDevice(b->device));
   const int W = b->count * params->starts;
   const OutLayout L = out_layout(W, p_stride);
-  QAP_TRY(grow(&b->scratch, &b->scratch_bytes, L.total));
-  const qap_walk_outputs d = carve_outputs(static_cast<char*>(b->scratch), L, W);
+  const size_t freq_off = (L.total + 255) / 256 * 256;
+  const size_t freq_bytes = out->freq ? (size_t)W * p_stride * p_stride * 4 : 0;
+  QAP_TRY(grow(&b->scratch, &b->scratch_bytes, freq_off + freq_bytes));
+  qap_walk_outputs d = carve_outputs(static_cast<char*>(b->scratch), L, W);
+  if (out->freq) d.freq = reinterpret_cast<int32_t*>(static_cast<char*>(b->scratch) + freq_off);
   QAP_TRY(qap_batch_search_async(b, params, &d, p_stride, b->stream));
   return copy_outputs_back(out, d, W, p_stride, b->stream);
 }

@@ -225,8 +225,11 @@ inline qap_status prepare_kernel(const void* fn, int smem) {
   int dev = 0, optin = 0;
   QAP_CUDA(cudaGetDevice(&dev));
   QAP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (smem > optin) return QAP_EUNSUPPORTED;
-  QAP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  cudaFuncAttributes fa{};
+  QAP_CUDA(cudaFuncGetAttributes(&fa, fn));
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;  // the static part counts too
+  if (smem > dyn_max) return QAP_EUNSUPPORTED;
+  QAP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
   done.push_back(fn);
   return QAP_OK;
 }
@@ -244,9 +247,11 @@ inline qap_status validate_params(const qap_search_params* p) {
   }
   if (p->launch != QAP_LAUNCH_PERSISTENT && p->launch != QAP_LAUNCH_PLAIN) return QAP_EINVAL;
   if (p->tenure_per_n != 0 && p->tenure_per_n != 1) return QAP_EINVAL;
+  // the kernel forms tmax * n + 99 and period * n in 32-bit integers
   if (p->tenure_per_n && p->iters > 0 &&
-      ((int64_t)p->tenure.tmax * kMaxN / 10 + 1 + p->iters >= (int64_t)INT_MAX ||
-       (int64_t)p->tenure.period * kMaxN > (int64_t)INT_MAX))
+      ((int64_t)p->tenure.tmax * kMaxN + 99 > (int64_t)INT_MAX ||
+       (int64_t)p->tenure.period * kMaxN > (int64_t)INT_MAX ||
+       (int64_t)p->tenure.tmax * kMaxN / 100 + 1 + p->iters >= (int64_t)INT_MAX))
     return QAP_EINVAL;
   const int t = p->threads_per_walk;
   if (t != 0 && t != 128 && t != 256 && t != 512 && t != 1024) return QAP_EINVAL;
@@ -276,6 +281,7 @@ inline qapk::SearchArgs make_search_args(const qap_search_params* p, const qap_w
   a.descent_moves = o->descent_moves;
   a.hash = o->hash;
   a.descent_hash = o->descent_hash;
+  a.freq = o->freq;
   return a;
 }
 
@@ -348,6 +354,7 @@ inline qap_status copy_outputs_back(const qap_walk_outputs* out, const qap_walk_
   QAP_CUDA(d2h(out->iters_done, d.iters_done, (size_t)W * 4));
   QAP_CUDA(d2h(out->status, d.status, (size_t)W * 4));
   QAP_CUDA(d2h(out->descent_moves, d.descent_moves, (size_t)W * 4));
+  QAP_CUDA(d2h(out->freq, d.freq, (size_t)W * p_stride * p_stride * 4));
   QAP_CUDA(cudaStreamSynchronize(s));
   return QAP_OK;
 }

@@ -64,7 +64,7 @@ struct SearchArgs {
   uint64_t seed;
   int descend, max_descent, iters;
   int tmin, tmax, period, aspiration;
-  int tenure_per_n;   // tmin, tmax, period in tenths of the instance's n
+  int tenure_per_n;   // tmin, tmax, period in hundredths of the instance's n
   int p_stride;       // elements per best_p row
   int32_t* best_p;
   int64_t* best_cost;
@@ -75,6 +75,7 @@ struct SearchArgs {
   int32_t* descent_moves;
   uint64_t* hash;
   uint64_t* descent_hash;
+  int32_t* freq;      // p_stride x p_stride per row, or null
 };
 
 // Walks of one instance.
@@ -778,11 +779,18 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   }
 
   // ---- tabu search (Sections 4.3, 4.4).
+  // frequency memory of this walk (Section 4.3): zeroed here, then the owner
+  // of each applied move adds one at [s][r]
+  int32_t* fq = a.freq ? a.freq + (size_t)row * a.p_stride * a.p_stride : nullptr;
+  if (fq) {
+    for (int c = tid; c < a.p_stride * a.p_stride; c += NT) fq[c] = 0;
+    __syncthreads();
+  }
   int tmin = a.tmin, tmax = a.tmax, period = a.period;
   if (a.tenure_per_n) {
-    tmin = max(1, a.tmin * n / 10);
-    tmax = max(tmin, (a.tmax * n + 9) / 10);
-    period = a.period * n / 10;
+    tmin = max(1, a.tmin * n / 100);
+    tmax = max(tmin, (a.tmax * n + 99) / 100);
+    period = a.period * n / 100;
   }
   DT best = cur;
   int best_iter = 0, status = 0, done = 0;
@@ -835,6 +843,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       stamp = it + tmin + (int)below(x, (uint32_t)(tmax - tmin + 1));
     }
     update_and_scan(r, s, true, it + 1, stamp, cur, best, bd, bk);
+    if (fq && su == r && s >= sv && s < sv + slen) atomicAdd(fq + s * a.p_stride + r, 1);
     swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
     DT* t = gc; gc = gn; gn = t;
   }

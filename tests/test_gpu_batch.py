@@ -67,7 +67,7 @@ def test_tenure_per_n_matches_each_instance_rule():
         Ds.append(D)
     W = 3
     with q.Batch(Fs, Ds) as b:
-        g = b.search(q.make_params(W, seed=8, iters=300, tenure=(9, 11, 20), tenure_per_n=True))
+        g = b.search(q.make_params(W, seed=8, iters=300, tenure=(90, 110, 200), tenure_per_n=True))
     for i in range(3):
         check_instance(g, i, W, Fs[i], Ds[i], seed=8, iters=300,
                        tenure=instances.baseline_tenure(Fs[i].shape[0]))
@@ -129,7 +129,7 @@ def test_full_batch512_sampled_walks():
     W, iters = w["walks"], w["iters"]
     # each instance's own tenure rule: [0.9n, 1.1n] redrawn every 2n
     with q.Batch([i.F for i in insts], [i.D for i in insts], force_int64=True) as b:
-        g = b.search(q.make_params(W, seed=w["seed"], iters=iters, tenure=(9, 11, 20),
+        g = b.search(q.make_params(W, seed=w["seed"], iters=iters, tenure=(90, 110, 200),
                                    tenure_per_n=True))
     assert (g["iters_done"] == iters).all() and (g["status"] == 0).all()
     rng = np.random.default_rng(0)
@@ -156,7 +156,7 @@ def test_batch_with_large_instances_uses_workspace():
         Fs.append(F)
         Ds.append(D)
     W = 2
-    prm = q.make_params(W, seed=4, iters=50, tenure=(9, 11, 20), tenure_per_n=True)
+    prm = q.make_params(W, seed=4, iters=50, tenure=(90, 110, 200), tenure_per_n=True)
     with q.Batch(Fs, Ds) as b:
         assert b.plan(prm)["pairs_per_thread"] == 40
         g = b.search(prm)

@@ -29,7 +29,7 @@ def _batch():
 
 def test_noalloc_equals_batch_search_on_two_calls(torch):
     W = 4
-    prm = q.make_params(W, seed=77, iters=300, tenure=(9, 11, 20), tenure_per_n=True,
+    prm = q.make_params(W, seed=77, iters=300, tenure=(90, 110, 200), tenure_per_n=True,
                         descend=True)
     with _batch() as b:
         stream = torch.cuda.Stream()
