@@ -23,6 +23,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 REF, FAST, CHECK = 0, 1, 2
+TABU_PAIR, TABU_UNIT_LOC, TABU_UNIT = 0, 1, 2
 OK, EOVERFLOW, EINVAL, EMISMATCH = 0, 1, 2, 3
 STREAM_START, STREAM_TENURE = 0, 1
 
@@ -47,6 +48,10 @@ def build(force: bool = False) -> str:
 class _Tenure(ctypes.Structure):
     _fields_ = [("tmin", ctypes.c_int32), ("tmax", ctypes.c_int32),
                 ("period", ctypes.c_int32)]
+
+
+class _Rules(ctypes.Structure):
+    _fields_ = [("criterion", ctypes.c_int32), ("penalty", ctypes.c_int32)]
 
 
 class _WalkResult(ctypes.Structure):
@@ -85,11 +90,11 @@ def lib():
             L.orc_2opt.argtypes = [vp, vp, ctypes.c_int, vp, i32, ctypes.c_int, vp, i32,
                                    ctypes.POINTER(_WalkResult)]
             L.orc_tabu.argtypes = [vp, vp, ctypes.c_int, vp, i32, ctypes.POINTER(_Tenure),
-                                   ctypes.c_int, u64, u32, ctypes.c_int, vp, vp, vp,
-                                   ctypes.POINTER(_WalkResult)]
+                                   ctypes.c_int, ctypes.POINTER(_Rules), u64, u32, ctypes.c_int,
+                                   vp, vp, vp, ctypes.POINTER(_WalkResult)]
             L.orc_run_walks.argtypes = [vp, vp, ctypes.c_int, i32, vp, vp, ctypes.c_int, i32,
-                                        i32, ctypes.POINTER(_Tenure), ctypes.c_int, u64,
-                                        ctypes.c_int, ctypes.c_int,
+                                        i32, ctypes.POINTER(_Tenure), ctypes.c_int,
+                                        ctypes.POINTER(_Rules), u64, ctypes.c_int, ctypes.c_int,
                                         vp, vp, vp, vp, vp, vp, vp, vp, vp]
             L.orc_brute_force.argtypes = [vp, vp, ctypes.c_int, vp, vp]
             L.orc_brute_force.restype = i64
@@ -188,10 +193,12 @@ def two_opt(F, D, p, max_iters=-1, mode=FAST, moves_cap=0):
 
 
 def tabu(F, D, p, iters, tmin, tmax, period, aspiration, seed, walk, mode=FAST,
-         want_freq=False):
+         want_freq=False, criterion=TABU_PAIR, penalty=0):
     """Tabu search from p; returns (final_p, best_p, result dict[, freq]).
 
-    The dict holds ``moves``, the applied moves as (r, s) rows."""
+    The dict holds ``moves``, the applied moves as (r, s) rows.  ``criterion``
+    picks the tabu rule (TABU_PAIR, TABU_UNIT_LOC, TABU_UNIT) and ``penalty``
+    the frequency penalty on non-improving moves."""
     F = _mat(F); D = _mat(D, F.shape[0])
     n = F.shape[0]
     p = np.array(p, dtype=np.int32, copy=True)
@@ -200,8 +207,10 @@ def tabu(F, D, p, iters, tmin, tmax, period, aspiration, seed, walk, mode=FAST,
     mv = np.full((max(iters, 0), 2), -1, dtype=np.int32)
     res = _WalkResult()
     tn = _Tenure(tmin, tmax, period)
+    rules = _Rules(criterion, penalty)
     _check(lib().orc_tabu(_p(F), _p(D), n, _p(p), iters, ctypes.byref(tn), int(aspiration),
-                          seed, walk, mode, _p(best_p), _p(freq), _p(mv), ctypes.byref(res)))
+                          ctypes.byref(rules), seed, walk, mode, _p(best_p), _p(freq), _p(mv),
+                          ctypes.byref(res)))
     d = _res_dict(res)
     d["moves"] = mv[:d["iters_done"]]
     out = (p, best_p, d)
@@ -215,7 +224,7 @@ def _res_dict(res):
 
 def run_walks(F, D, walks, *, seed, iters=0, tenure=(1, 1, 0), aspiration=True,
               descend=False, max_descent=-1, walk_ids=None, starts=None, mode=FAST,
-              threads=0):
+              threads=0, criterion=TABU_PAIR, penalty=0):
     """Run `walks` independent searches of one instance (OpenMP over walks).
 
     Walk w draws its start permutation and tenures with walk id
@@ -245,9 +254,10 @@ def run_walks(F, D, walks, *, seed, iters=0, tenure=(1, 1, 0), aspiration=True,
         descent_moves=np.zeros(walks, dtype=np.int32),
     )
     tn = _Tenure(*tenure)
+    rules = _Rules(criterion, penalty)
     err = lib().orc_run_walks(
         _p(F), _p(D), n, walks, _p(ids), _p(st), int(descend), max_descent, iters,
-        ctypes.byref(tn), int(aspiration), seed, mode, threads,
+        ctypes.byref(tn), int(aspiration), ctypes.byref(rules), seed, mode, threads,
         _p(out["best_p"]), _p(out["best_cost"]), _p(out["final_cost"]), _p(out["best_iter"]),
         _p(out["iters_done"]), _p(out["status"]), _p(out["hash"]), _p(out["descent_hash"]),
         _p(out["descent_moves"]))

@@ -298,52 +298,88 @@ int orc_2opt(const int64_t *F, const int64_t *D, int n, int32_t *p,
 /* Tabu search (Sections 4.3, 4.4).  Iterations are numbered from 1.         */
 /* Per iteration:                                                            */
 /*   1. evaluate every pairwise exchange (Eq. 2);                            */
-/*   2. a move is admissible if it is not tabu (Tabuarr[r][s] <= it) or,    */
-/*      with aspiration on, if it leads to a cost strictly below the best    */
-/*      cost so far;                                                         */
-/*   3. take the admissible move of lowest delta, ties to the lowest (r, s)  */
+/*   2. a move is admissible if it is not tabu under the chosen criterion    */
+/*      (below) or, with aspiration on, if it leads to a cost strictly below */
+/*      the best cost so far;                                                */
+/*   3. take the admissible move of lowest score, ties to the lowest (r, s)  */
 /*      (the paper's "next lowest cost" loop over forbidden moves selects    */
-/*      exactly this);                                                       */
+/*      exactly this).  The score is the delta itself; with a frequency      */
+/*      penalty lambda > 0 a non-improving move (delta >= 0) scores          */
+/*      delta + lambda * (times the move was applied so far);               */
 /*   4. if no move is admissible the walk stops early (status 1);            */
-/*   5. apply it, set Tabuarr[r][s] = it + t (t from the tenure rule), count */
-/*      the exchange in the frequency memory (lower triangle of Tabuarr),   */
-/*      and keep the solution if its cost is strictly below the best.        */
-/* If start_from_2opt is set, the walk first descends with 2opt to a local   */
-/* minimum and the tabu phase starts there with its iteration count at 1.    */
+/*   5. apply it with a tenure t from the tenure rule, mark it tabu under    */
+/*      the criterion, count the exchange in the frequency memory (lower     */
+/*      triangle of Tabuarr) and keep the solution if its cost is strictly   */
+/*      below the best.                                                      */
+/*                                                                           */
+/* Tabu criteria (every mark is "until iteration it + t"; a mark m forbids   */
+/* while m > it):                                                            */
+/*   ORC_TABU_PAIR      the paper's Tabuarr (Section 4.3): the applied move  */
+/*                      (r, s) itself is forbidden;                          */
+/*   ORC_TABU_UNIT_LOC  Taillard's robust tabu search (1991, the elementary  */
+/*                      search Section 4.3 follows): units r and s may not   */
+/*                      return to the locations they leave; a move (u, v) is */
+/*                      forbidden when BOTH u would return to a forbidden    */
+/*                      location and v would;                                */
+/*   ORC_TABU_UNIT      Zhu et al.'s unit marking (Section 3.1): units r and */
+/*                      s are marked; a move is forbidden when EITHER of its */
+/*                      units is marked.                                     */
+/* The frequency penalty is the long-term frequency-based memory Section 7   */
+/* proposes as future work, in the usual form of a penalty on non-improving  */
+/* moves (Glover & Laguna, cited in Section 4.3).                            */
 /* ------------------------------------------------------------------------ */
+
+static int move_is_tabu(int crit, int n, const int32_t *p, int u, int v, int32_t it,
+                        const int32_t *pair_until, const int32_t *loc_until,
+                        const int32_t *unit_until) {
+  if (crit == ORC_TABU_PAIR) return pair_until[(size_t)u * n + v] > it;
+  if (crit == ORC_TABU_UNIT_LOC)  /* u would move to p[v], v to p[u] */
+    return loc_until[(size_t)u * n + p[v]] > it && loc_until[(size_t)v * n + p[u]] > it;
+  return unit_until[u] > it || unit_until[v] > it;
+}
 
 int orc_tabu(const int64_t *F, const int64_t *D, int n, int32_t *p,
              int32_t iters, const orc_tenure_t *tn, int aspiration,
-             uint64_t seed, uint32_t walk, int mode,
+             const orc_rules_t *rules, uint64_t seed, uint32_t walk, int mode,
              int32_t *best_p, int32_t *freq, int32_t *moves,
              orc_walk_result *res) {
+  const int crit = rules ? rules->criterion : ORC_TABU_PAIR;
+  const int64_t lambda = rules ? rules->penalty : 0;
+  if (crit < ORC_TABU_PAIR || crit > ORC_TABU_UNIT || lambda < 0) return ORC_EINVAL;
   int err = ORC_OK;
   delta_table t = {n, calloc((size_t)n * n, sizeof(int64_t))};
-  int32_t *tabu_until = calloc((size_t)n * n, sizeof(int32_t));
+  int32_t *pair_until = calloc((size_t)n * n, sizeof(int32_t)); /* [r][s], r < s  */
+  int32_t *loc_until = calloc((size_t)n * n, sizeof(int32_t));  /* [unit][location] */
+  int32_t *unit_until = calloc((size_t)n, sizeof(int32_t));     /* [unit]          */
+  int32_t *applied = calloc((size_t)n * n, sizeof(int32_t));    /* [r][s], r < s  */
   int64_t cur = orc_cost(F, D, n, p, &err);
   int64_t best = cur;
   int32_t best_iter = 0, status = 0, done = 0;
   uint64_t h = orc_hash_init();
   memcpy(best_p, p, sizeof(int32_t) * (size_t)n);
-  if (freq) memset(freq, 0, sizeof(int32_t) * (size_t)n * n);
   table_fill(&t, F, D, p, &err);
   for (int32_t it = 1; it <= iters && !err; ++it) {
     int br = -1, bs = -1;
-    int64_t bd = 0;
+    int64_t bd = 0, bscore = 0;
     for (int r = 0; r < n; ++r)
       for (int s = r + 1; s < n; ++s) {
         int64_t d = t.dl[(size_t)r * n + s];
-        int not_tabu = tabu_until[(size_t)r * n + s] <= it;
+        int not_tabu = !move_is_tabu(crit, n, p, r, s, it, pair_until, loc_until, unit_until);
         int aspires = aspiration && chk_add(cur, d, &err) < best;
         if (!(not_tabu || aspires)) continue;
-        if (br < 0 || d < bd) { br = r; bs = s; bd = d; }
+        int64_t score = d;
+        if (d >= 0) score = chk_add(d, chk_mul(lambda, applied[(size_t)r * n + s], &err), &err);
+        if (br < 0 || score < bscore) { br = r; bs = s; bd = d; bscore = score; }
       }
     if (br < 0) { status = 1; break; }
     int32_t tenure = orc_tenure(tn, seed, walk, it);
+    pair_until[(size_t)br * n + bs] = it + tenure;
+    loc_until[(size_t)br * n + p[br]] = it + tenure;  /* the locations they leave */
+    loc_until[(size_t)bs * n + p[bs]] = it + tenure;
+    unit_until[br] = unit_until[bs] = it + tenure;
+    applied[(size_t)br * n + bs] += 1;
     apply_swap(p, br, bs);
     cur = chk_add(cur, bd, &err);
-    tabu_until[(size_t)br * n + bs] = it + tenure;
-    if (freq) freq[(size_t)bs * n + br] += 1;
     h = orc_hash_move(h, br, bs);
     if (moves) { moves[2 * (it - 1)] = br; moves[2 * (it - 1) + 1] = bs; }
     done = it;
@@ -354,8 +390,16 @@ int orc_tabu(const int64_t *F, const int64_t *D, int n, int32_t *p,
     }
     table_update(&t, F, D, p, br, bs, mode, &err);
   }
+  if (freq) { /* lower triangle: [s][r] counts move (r, s) */
+    memset(freq, 0, sizeof(int32_t) * (size_t)n * n);
+    for (int r = 0; r < n; ++r)
+      for (int s = r + 1; s < n; ++s) freq[(size_t)s * n + r] = applied[(size_t)r * n + s];
+  }
   free(t.dl);
-  free(tabu_until);
+  free(pair_until);
+  free(loc_until);
+  free(unit_until);
+  free(applied);
   res->best_cost = best;
   res->final_cost = cur;
   res->best_iter = best_iter;
@@ -381,8 +425,8 @@ int orc_tabu(const int64_t *F, const int64_t *D, int n, int32_t *p,
 int orc_run_walks(const int64_t *F, const int64_t *D, int n, int32_t walks,
                   const uint32_t *walk_ids, const int32_t *starts,
                   int descend, int32_t max_descent, int32_t iters,
-                  const orc_tenure_t *tn, int aspiration, uint64_t seed,
-                  int mode, int threads,
+                  const orc_tenure_t *tn, int aspiration, const orc_rules_t *rules,
+                  uint64_t seed, int mode, int threads,
                   int32_t *best_p, int64_t *best_cost, int64_t *final_cost,
                   int32_t *best_iter, int32_t *iters_done, int32_t *status,
                   uint64_t *hash, uint64_t *descent_hash, int32_t *descent_moves) {
@@ -406,7 +450,7 @@ int orc_run_walks(const int64_t *F, const int64_t *D, int n, int32_t walks,
       dh = r2.hash;
     }
     if (!err && (iters > 0 || !descend)) {
-      err = orc_tabu(F, D, n, p, iters, tn, aspiration, seed, wid, mode,
+      err = orc_tabu(F, D, n, p, iters, tn, aspiration, rules, seed, wid, mode,
                      best_p + (size_t)w * n, NULL, NULL, &rt);
     } else if (!err) {
       memcpy(best_p + (size_t)w * n, p, sizeof(int32_t) * (size_t)n);

@@ -17,6 +17,10 @@ enum { ORC_STREAM_START = 0, ORC_STREAM_TENURE = 1 };
 
 typedef struct { int32_t tmin, tmax, period; } orc_tenure_t;
 
+/* Tabu criterion and frequency penalty of the tabu phase (see orc_tabu). */
+enum { ORC_TABU_PAIR = 0, ORC_TABU_UNIT_LOC = 1, ORC_TABU_UNIT = 2 };
+typedef struct { int32_t criterion; int32_t penalty; } orc_rules_t;
+
 typedef struct {
   int64_t best_cost;
   int64_t final_cost;
@@ -43,14 +47,14 @@ int orc_2opt(const int64_t *F, const int64_t *D, int n, int32_t *p,
              orc_walk_result *res);
 int orc_tabu(const int64_t *F, const int64_t *D, int n, int32_t *p,
              int32_t iters, const orc_tenure_t *tn, int aspiration,
-             uint64_t seed, uint32_t walk, int mode,
+             const orc_rules_t *rules, uint64_t seed, uint32_t walk, int mode,
              int32_t *best_p, int32_t *freq, int32_t *moves,
              orc_walk_result *res);
 int orc_run_walks(const int64_t *F, const int64_t *D, int n, int32_t walks,
                   const uint32_t *walk_ids, const int32_t *starts,
                   int descend, int32_t max_descent, int32_t iters,
-                  const orc_tenure_t *tn, int aspiration, uint64_t seed,
-                  int mode, int threads,
+                  const orc_tenure_t *tn, int aspiration, const orc_rules_t *rules,
+                  uint64_t seed, int mode, int threads,
                   int32_t *best_p, int64_t *best_cost, int64_t *final_cost,
                   int32_t *best_iter, int32_t *iters_done, int32_t *status,
                   uint64_t *hash, uint64_t *descent_hash, int32_t *descent_moves);

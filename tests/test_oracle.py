@@ -477,6 +477,165 @@ def test_run_walks_matches_single_walks(orc):
 
 
 # ---------------------------------------------------------------------------
+# Other tabu criteria (Taillard's unit-location rule, Zhu et al.'s unit
+# marking, Section 3.1) and the frequency penalty (Section 7's long-term
+# memory).  Replayed by brute force on Eq. 1 differences with bookkeeping of
+# their own, and pinned by hand-derived trajectories on instances whose
+# every delta is zero (constant off-diagonal distances).
+# ---------------------------------------------------------------------------
+
+def replay_rules(orc, F, D, p0, moves, iters, tn, aspiration, seed, walk, criterion, penalty):
+    n = len(p0)
+    p = np.array(p0)
+    cur = orc.cost(F, D, p)
+    best = cur
+    pair_until, barred, marked, count = {}, {}, {}, {}
+    for it in range(1, iters + 1):
+        cand = []
+        for a in range(n):
+            for b in range(a + 1, n):
+                dlt = orc.cost(F, D, swapped(p, a, b)) - cur
+                if criterion == orc.TABU_PAIR:
+                    forbidden = pair_until.get((a, b), 0) > it
+                elif criterion == orc.TABU_UNIT_LOC:
+                    # a would move to b's location and b to a's
+                    forbidden = (barred.get((a, p[b]), 0) > it and barred.get((b, p[a]), 0) > it)
+                else:
+                    forbidden = marked.get(a, 0) > it or marked.get(b, 0) > it
+                if forbidden and not (aspiration and cur + dlt < best):
+                    continue
+                rank = dlt + penalty * count.get((a, b), 0) if dlt >= 0 else dlt
+                cand.append((rank, a, b, dlt))
+        if not cand:
+            assert len(moves) == it - 1
+            return best, 1
+        _, a, b, dlt = min(cand)
+        assert tuple(moves[it - 1]) == (a, b), f"iteration {it}"
+        until = it + orc.tenure(*tn, seed, walk, it)
+        pair_until[(a, b)] = until
+        barred[(a, p[a])] = until
+        barred[(b, p[b])] = until
+        marked[a] = marked[b] = until
+        count[(a, b)] = count.get((a, b), 0) + 1
+        p = swapped(p, a, b)
+        cur += dlt
+        best = min(best, cur)
+    assert len(moves) == iters
+    return best, 0
+
+
+@pytest.mark.parametrize("criterion", [1, 2])
+@pytest.mark.parametrize("penalty,asp,tn", [(0, True, (1, 3, 0)), (0, False, (2, 2, 5)),
+                                            (4, True, (1, 2, 0)), (50, False, (1, 3, 4))])
+def test_rules_moves_follow_definitions(orc, criterion, penalty, asp, tn):
+    rng = np.random.default_rng(30 + 7 * criterion + penalty)
+    n, iters = 7, 50
+    F, D = rand_instance(rng, n, lo=0, hi=12, diag=False)
+    seed, walk = 8, 3
+    p0 = orc.start_perm(seed, walk, n)
+    p, best_p, res, freq = orc.tabu(F, D, p0, iters, *tn, asp, seed, walk, want_freq=True,
+                                    criterion=criterion, penalty=penalty)
+    best, status = replay_rules(orc, F, D, p0, res["moves"], iters, tn, asp, seed, walk,
+                                criterion, penalty)
+    assert (res["best_cost"], res["status"]) == (best, status)
+    assert res["final_cost"] == orc.cost(F, D, p) and orc.cost(F, D, best_p) == best
+    assert freq.sum() == res["iters_done"]
+
+
+def test_penalty_moves_follow_definition_pair_criterion(orc):
+    rng = np.random.default_rng(41)
+    n, iters, tn = 6, 80, (1, 2, 0)
+    F, D = rand_instance(rng, n, lo=-5, hi=9)
+    p0 = orc.start_perm(2, 0, n)
+    _, _, res = orc.tabu(F, D, p0, iters, *tn, True, 2, 0, penalty=7)
+    best, status = replay_rules(orc, F, D, p0, res["moves"], iters, tn, True, 2, 0, 0, 7)
+    assert (res["best_cost"], res["status"]) == (best, status)
+
+
+def constant_distance_instance(rng, n, c=7):
+    """Every permutation costs c * sum of off-diagonal F: every delta is 0."""
+    F, _ = rand_instance(rng, n, lo=0, hi=9, diag=False)
+    D = np.full((n, n), c, dtype=np.int64)
+    np.fill_diagonal(D, 0)
+    return F, D
+
+
+def test_unit_marking_stops_after_disjoint_pairs(orc):
+    # Every delta is 0, so the lowest free pair is taken.  With a long
+    # tenure each move marks two fresh units: (0,1), (2,3), (4,5), then only
+    # unit 6 is free and no move is allowed.
+    F, D = constant_distance_instance(np.random.default_rng(42), 7)
+    _, _, res = orc.tabu(F, D, np.arange(7), 20, 100, 100, 0, False, 1, 0,
+                         criterion=orc.TABU_UNIT)
+    assert res["moves"].tolist() == [[0, 1], [2, 3], [4, 5]]
+    assert res["status"] == 1 and res["iters_done"] == 3
+
+
+def test_unit_marking_tenure_two_alternates(orc):
+    # A mark set at it lasts through it + 1, so (0,1) and (2,3) alternate.
+    F, D = constant_distance_instance(np.random.default_rng(43), 6)
+    _, _, res = orc.tabu(F, D, np.arange(6), 8, 2, 2, 0, False, 1, 0, criterion=orc.TABU_UNIT)
+    assert res["moves"].tolist() == [[0, 1], [2, 3]] * 4 and res["status"] == 0
+
+
+def test_unit_location_hand_trajectory(orc):
+    # n = 3, identity start, every delta 0, long tenure, no aspiration.
+    # it 1: (0,1); units 0, 1 barred from locations 0, 1.  it 2: (0,1) would
+    # return both, (0,2) sends unit 0 to location 2: taken.  it 3: (0,1)
+    # sends unit 1 to location 2, never left: taken.  it 4: (0,1) returns
+    # both, (0,2) sends unit 2 to location 0: taken.  it 5: every move
+    # returns both of its units: the walk stops.
+    F, D = constant_distance_instance(np.random.default_rng(44), 3)
+    _, _, res = orc.tabu(F, D, np.arange(3), 10, 100, 100, 0, False, 1, 0,
+                         criterion=orc.TABU_UNIT_LOC)
+    assert res["moves"].tolist() == [[0, 1], [0, 2], [0, 1], [0, 2]]
+    assert res["status"] == 1
+
+
+def test_frequency_penalty_round_robin(orc):
+    # Every delta is 0 and a tenure of 1 forbids nothing, so with the
+    # penalty the least-applied pair is taken, lowest first: a round robin
+    # over the 6 pairs of n = 4 in lexicographic order.
+    F, D = constant_distance_instance(np.random.default_rng(45), 4)
+    pairs = [[a, b] for a in range(4) for b in range(a + 1, 4)]
+    _, _, res, freq = orc.tabu(F, D, np.arange(4), 14, 1, 1, 0, True, 1, 0, want_freq=True,
+                               penalty=1)
+    assert res["moves"].tolist() == [pairs[k % 6] for k in range(14)]
+    assert sorted(freq[np.tril_indices(4, -1)].tolist()) == [2, 2, 2, 2, 3, 3]
+    # without the penalty the same search repeats the lowest pair
+    _, _, res0 = orc.tabu(F, D, np.arange(4), 14, 1, 1, 0, True, 1, 0)
+    assert res0["moves"].tolist() == [[0, 1]] * 14
+
+
+def test_penalty_leaves_improving_moves_alone(orc):
+    # Improving moves are ranked by their delta alone, so a heavy penalty
+    # follows the unpenalised search for as long as that one improves.
+    rng = np.random.default_rng(46)
+    n = 12
+    F, D = rand_instance(rng, n, lo=0, hi=50, diag=False)
+    p0 = orc.start_perm(4, 1, n)
+    _, _, plain = orc.tabu(F, D, p0, 60, 3, 5, 0, True, 4, 1)
+    _, _, heavy = orc.tabu(F, D, p0, 60, 3, 5, 0, True, 4, 1, penalty=10**6)
+    costs, p, k = [], np.array(p0), 0
+    for (a, b) in plain["moves"]:
+        q = swapped(p, a, b)
+        if orc.cost(F, D, q) >= orc.cost(F, D, p):
+            break
+        p, k = q, k + 1
+    assert k >= 3
+    assert np.array_equal(heavy["moves"][:k], plain["moves"][:k])
+    assert not np.array_equal(heavy["moves"], plain["moves"])
+
+
+def test_rules_reject_bad_arguments(orc):
+    F, D = constant_distance_instance(np.random.default_rng(47), 4)
+    with pytest.raises(ValueError):
+        orc.tabu(F, D, np.arange(4), 5, 1, 1, 0, True, 1, 0, criterion=3)
+    with pytest.raises(ValueError):
+        orc.tabu(F, D, np.arange(4), 5, 1, 1, 0, True, 1, 0, penalty=-1)
+
+
+# ---------------------------------------------------------------------------
 # stored oracle outputs (written by tests/golden/make_golden.py)
 # ---------------------------------------------------------------------------
 
