@@ -84,6 +84,22 @@ typedef struct {
 #define QAP_LAUNCH_PERSISTENT 0  /* one launch; CTAs loop over walks          */
 #define QAP_LAUNCH_PLAIN 1       /* one launch per walk (comparison form)     */
 
+/* Tabu criteria.  Applying move (r, s) at iteration it with tenure t marks
+ * something "until it + t"; a mark m forbids while m > it.
+ *   QAP_TABU_PAIR      the paper's Tabuarr (Section 4.3): move (r, s) itself
+ *                      is forbidden.
+ *   QAP_TABU_UNIT_LOC  Taillard's robust tabu search (1991), the elementary
+ *                      search Section 4.3 follows: units r and s may not
+ *                      return to the locations they leave; a move (u, v) is
+ *                      forbidden when both u and v would return to a
+ *                      location they are barred from.
+ *   QAP_TABU_UNIT      Zhu et al.'s unit marking (Section 3.1): units r and s
+ *                      are marked; a move is forbidden when either of its
+ *                      units is marked. */
+#define QAP_TABU_PAIR 0
+#define QAP_TABU_UNIT_LOC 1
+#define QAP_TABU_UNIT 2
+
 typedef struct {
   int32_t n;
   int32_t delta_bytes;     /* 4 (int32 path) or 8 (int64 path)              */
@@ -146,6 +162,22 @@ typedef struct {
                               period' = floor(period n / 100);
                               e.g. (10, 33, 0) is the paper's [0.1n, 0.33n]
                               drawn per move; 0: absolute                    */
+  int32_t criterion;       /* QAP_TABU_PAIR (default), _UNIT_LOC or _UNIT    */
+  int32_t freq_penalty;    /* lambda >= 0: frequency-based diversification,
+                              the long-term memory Section 7 proposes.  A
+                              non-improving move (delta >= 0) is ranked by
+                              delta + lambda * (times the walk applied it in
+                              its tabu phase); improving moves by delta.
+                              Aspiration and the cost use the plain delta.
+                              0 = off.  With int32 deltas the context's
+                              bound B + lambda * iters must stay below 2^31
+                              - 1, else QAP_EOVERFLOW (create the context
+                              with QAP_FORCE_INT64).  criterion != PAIR or
+                              lambda > 0 use a per-CTA device workspace of
+                              (2 n^2 + n) int32 (not available to
+                              qap_batch_search_noalloc: QAP_EUNSUPPORTED).
+                              The serving loop picks int64 deltas itself
+                              when the penalty needs them.                   */
 } qap_search_params;
 
 /* Per-walk outputs; every pointer may be NULL except best_cost.  For

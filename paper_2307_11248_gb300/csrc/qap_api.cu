@@ -245,6 +245,7 @@ qap_status qap_search_async(qap_ctx* ctx, const qap_search_params* params,
   if (!ctx) return QAP_EINVAL;
   QAP_TRY(validate_params(params));
   if (!out || !out->best_cost) return QAP_EINVAL;
+  QAP_TRY(check_penalty(params, ctx->dbytes, ctx->di.bound));
   QAP_CUDA(cudaSetDevice(ctx->device));
   Launch L;
   QAP_TRY(plan_ctx(ctx, params, &L));
@@ -255,7 +256,8 @@ qap_status qap_search_async(qap_ctx* ctx, const qap_search_params* params,
   a.starts = d_starts;
   a.walks = params->starts;
   a.walk_offset = 0;
-  a.ws_stride = workspace_per_cta(L.plan, ctx->dbytes);
+  a.ws_stride = workspace_per_cta(L.plan, ctx->dbytes, ctx->di.n, params);
+  a.s.rws_off = delta_workspace(L.plan, ctx->dbytes);
   if (a.ws_stride) {
     // the plain form runs one CTA per launch; launches on one stream share it
     const int ctas = params->launch == QAP_LAUNCH_PLAIN ? 1 : L.grid;
@@ -474,6 +476,7 @@ qap_status qap_batch_search_async(qap_batch* b, const qap_search_params* params,
   QAP_TRY(validate_params(params));
   if (!out || !out->best_cost || p_stride < b->nmax) return QAP_EINVAL;
   if (params->launch != QAP_LAUNCH_PERSISTENT) return QAP_EINVAL;
+  for (const DevInstance& d : b->di) QAP_TRY(check_penalty(params, b->dbytes, d.bound));
   QAP_CUDA(cudaSetDevice(b->device));
   Launch L;
   QAP_TRY(plan_batch(b, params, &L));
@@ -488,7 +491,8 @@ qap_status qap_batch_search_async(qap_batch* b, const qap_search_params* params,
   a.items = items;
   a.counter = b->d_counter;
   a.s = make_search_args(params, out, p_stride);
-  a.ws_stride = workspace_per_cta(L.plan, b->dbytes);
+  a.ws_stride = workspace_per_cta(L.plan, b->dbytes, b->nmax, params);
+  a.s.rws_off = delta_workspace(L.plan, b->dbytes);
   if (a.ws_stride) {
     QAP_TRY(grow(&b->ws, &b->ws_bytes, a.ws_stride * L.grid));
     a.ws = static_cast<unsigned char*>(b->ws);
@@ -575,6 +579,12 @@ extern "C" qap_status qap_batch_search_noalloc(qap_batch* b, const qap_search_pa
   QAP_TRY(validate_params(params));
   if (!out || !out->best_cost || p_stride < b->nmax) return QAP_EINVAL;
   if (params->launch != QAP_LAUNCH_PERSISTENT) return QAP_EINVAL;
+  if (uses_rule_tables(params)) {
+    snprintf(g_last_error, sizeof(g_last_error),
+             "qap_batch_search_noalloc: the unit criteria and the frequency penalty keep "
+             "per-CTA tables in an allocated workspace");
+    return QAP_EUNSUPPORTED;
+  }
   const int64_t items = (int64_t)b->count * params->starts;
   if (b->count > kNoallocMaxInstances || items > kNoallocMaxItems) {
     snprintf(g_last_error, sizeof(g_last_error),

@@ -206,10 +206,32 @@ inline bool choose_plan_fit(int nmax, int threads, const DevInstance* d, int cou
   return true;
 }
 
-inline size_t workspace_per_cta(const Plan& p, int dbytes) {
+// Per-CTA workspace: the deltas and marks of large-n plans, then the tables
+// of the other tabu criteria and of the frequency penalty when a search
+// uses them (loc_until n x n, unit_until n, applied n x n; int32).
+inline size_t delta_workspace(const Plan& p, int dbytes) {
   if (!(p.store & qapk::kGlobalDelta)) return 0;
   const size_t b = (size_t)p.nt * p.maxpt * ((size_t)dbytes + 4);
   return (b + 255) / 256 * 256;
+}
+
+inline bool uses_rule_tables(const qap_search_params* sp) {
+  return sp->iters > 0 && (sp->criterion != QAP_TABU_PAIR || sp->freq_penalty != 0);
+}
+
+inline size_t workspace_per_cta(const Plan& p, int dbytes, int nmax,
+                                const qap_search_params* sp) {
+  size_t b = delta_workspace(p, dbytes);
+  if (uses_rule_tables(sp)) b += ((size_t)(2 * nmax * nmax + nmax) * 4 + 255) / 256 * 256;
+  return b;
+}
+
+// With the frequency penalty a non-improving move's rank is delta + lambda *
+// count, count <= iters; int32 deltas must hold it below their sentinel.
+inline qap_status check_penalty(const qap_search_params* sp, int dbytes, int64_t bound) {
+  if (sp->freq_penalty == 0 || sp->iters == 0 || dbytes == 8) return QAP_OK;
+  const int64_t top = bound + (int64_t)sp->freq_penalty * sp->iters;
+  return top < (int64_t)INT32_MAX - 1 ? QAP_OK : QAP_EOVERFLOW;
 }
 
 extern std::mutex g_attr_mu;
@@ -246,6 +268,8 @@ inline qap_status validate_params(const qap_search_params* p) {
     if ((int64_t)p->iters + (int64_t)p->tenure.tmax >= (int64_t)INT_MAX) return QAP_EINVAL;
   }
   if (p->launch != QAP_LAUNCH_PERSISTENT && p->launch != QAP_LAUNCH_PLAIN) return QAP_EINVAL;
+  if (p->criterion < QAP_TABU_PAIR || p->criterion > QAP_TABU_UNIT || p->freq_penalty < 0)
+    return QAP_EINVAL;
   if (p->tenure_per_n != 0 && p->tenure_per_n != 1) return QAP_EINVAL;
   // the kernel forms tmax * n + 99 and period * n in 32-bit integers
   if (p->tenure_per_n && p->iters > 0 &&
@@ -271,6 +295,8 @@ inline qapk::SearchArgs make_search_args(const qap_search_params* p, const qap_w
   a.period = p->tenure.period;
   a.aspiration = p->aspiration;
   a.tenure_per_n = p->tenure_per_n;
+  a.crit = p->criterion;
+  a.lambda = p->freq_penalty;
   a.p_stride = p_stride;
   a.best_p = o->best_p;
   a.best_cost = o->best_cost;

@@ -39,6 +39,7 @@
 #pragma once
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "qap_philox.cuh"
 
@@ -65,6 +66,9 @@ struct SearchArgs {
   int descend, max_descent, iters;
   int tmin, tmax, period, aspiration;
   int tenure_per_n;   // tmin, tmax, period in hundredths of the instance's n
+  int crit;           // tabu criterion: 0 pair (r, s), 1 unit-location, 2 unit
+  int lambda;         // frequency penalty on non-improving moves (0 = off)
+  size_t rws_off;     // offset of the criterion/penalty tables in a CTA's workspace
   int p_stride;       // elements per best_p row
   int32_t* best_p;
   int64_t* best_cost;
@@ -705,8 +709,21 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   // Owners' pass after move (r, s): new deltas, then the scan for the next
   // iteration `nit` (tabu phase) or the next descent step.  Branch-free per
   // slot so the shared-memory loads of all slots are in flight together.
-  auto update_and_scan = [&](int r, int s, bool tabu, int nit, int stamp, DT ncur, DT nbest,
-                             DT& bd, uint32_t& bk) {
+  // Tables of the other tabu criteria and of the frequency penalty, in the
+  // CTA's workspace: loc_until[unit][location] (n x n), unit_until[unit] (n)
+  // and applied[r][s] (n x n, the penalty's counts, row-major so that a
+  // segment's are contiguous).  Addressed from the launch arguments when
+  // used so that they hold no registers in the paper's own search.
+  auto rule_tables = [&]() { return reinterpret_cast<int32_t*>(ws + a.rws_off); };
+  auto applied = [&]() { return rule_tables() + n * n + n; };
+
+  // With EXT (the other criteria or the frequency penalty in use) and a
+  // penalty lambda, a non-improving pair is ranked by delta + lambda *
+  // (times applied).
+  auto update_and_scan = [&](auto ext, int r, int s, bool tabu, int nit, int stamp, DT ncur,
+                             DT nbest, DT& bd, uint32_t& bk) {
+    constexpr bool EXT = decltype(ext)::value;
+    const int32_t* crow = EXT ? applied() + su * n : nullptr;
     using VO = VecOps<FE>;
     const auto* vec = reinterpret_cast<const typename VO::V*>(S.vec);
     const DT gr = gn[r], gs = gn[s];
@@ -739,8 +756,10 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       // loop so no shared-memory store sits between the slots' loads
       const int tb = isrs ? stamp : tbl;
       const bool adm = !tabu || tb <= nit || (a.aspiration && ncur + d < nbest);
-      if (valid && adm && d < bd) {
-        bd = d;
+      DT sc = d;
+      if constexpr (EXT) sc = d >= 0 ? d + (DT)a.lambda * (DT)crow[v] : d;
+      if (valid && adm && sc < bd) {
+        bd = sc;
         bk = ukey | (uint32_t)v;
       }
     }
@@ -770,7 +789,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       if (warp0) dh = fnv_step(dh, r, s);
       phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
       __syncthreads();
-      update_and_scan(r, s, false, 0, 0, cur, cur, bd, bk);
+      update_and_scan(std::false_type{}, r, s, false, 0, 0, cur, cur, bd, bk);
       swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
       DT* t = gc; gc = gn; gn = t;
     }
@@ -782,10 +801,20 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   // frequency memory of this walk (Section 4.3): zeroed here, then the owner
   // of each applied move adds one at [s][r]
   int32_t* fq = a.freq ? a.freq + (size_t)row * a.p_stride * a.p_stride : nullptr;
-  if (fq) {
+  if (fq)
     for (int c = tid; c < a.p_stride * a.p_stride; c += NT) fq[c] = 0;
-    __syncthreads();
+  // The other criteria keep each pair's mark ("until") in S.tabu as the
+  // paper's does: only the pairs touching r or s change it at a move.
+  const bool rules = a.iters > 0 && (a.crit != 0 || a.lambda != 0);
+  if (rules) {
+    int32_t* t = rule_tables();
+    for (int c = tid; c < 2 * n * n + n; c += NT) t[c] = 0;
   }
+  if (fq || rules) __syncthreads();
+  // locations of the move's units before it: S.sum's first two words (the
+  // block sum is done by now); written after the arg-min, read after the
+  // next barrier, before swap_rs can have moved them
+  int32_t* moved_from = reinterpret_cast<int32_t*>(S.sum);
   int tmin = a.tmin, tmax = a.tmax, period = a.period;
   if (a.tenure_per_n) {
     tmin = max(1, a.tmin * n / 100);
@@ -810,43 +839,96 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       }
     }
   }
-  for (int it = 1; it <= a.iters; ++it) {
-    block_argmin<DT, NT>(bd, bk, S.redD, S.redK);
-    if (copy_pending) {  // p after the previous iteration's move
-      for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
-      copy_pending = false;
+  // The iterations; EXT adds the other criteria and the penalty, so that
+  // the paper's own search runs a loop without their code.
+  auto tabu_loop = [&](auto ext) {
+    constexpr bool EXT = decltype(ext)::value;
+    for (int it = 1; it <= a.iters; ++it) {
+      block_argmin<DT, NT>(bd, bk, S.redD, S.redK);
+      if (copy_pending) {  // p after the previous iteration's move
+        for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
+        copy_pending = false;
+      }
+      if (bk == kNoMove) {
+        status = 1;
+        break;
+      }
+      const int r = (int)(bk >> 8), s = (int)(bk & 0xffu);
+      if constexpr (EXT) {
+        // bd is the move's rank; with the penalty a non-improving rank
+        // holds lambda * applied[r][s] on top of the delta
+        if (a.lambda != 0 && bd >= 0) bd -= (DT)a.lambda * (DT)applied()[r * n + s];
+        if (a.crit != 0 && tid == 0) {
+          moved_from[0] = S.perm[r];
+          moved_from[1] = S.perm[s];
+        }
+      }
+      cur += bd;
+      done = it;
+      if (warp0) h = fnv_step(h, r, s);
+      if (cur < best) {
+        best = cur;
+        best_iter = it;
+        copy_pending = true;
+      }
+      if (period > 0 && --tleft == 0) {  // it = 1, period + 1, ...
+        const uint32_t x = walk_draw(a.seed, wid, 1u, tdraw++);
+        tenure = tmin + (int)below(x, (uint32_t)(tmax - tmin + 1));
+        tleft = period;
+      }
+      phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
+      __syncthreads();
+      int stamp = it + tenure;
+      const bool owner = su == r && s >= sv && s < sv + slen;
+      if (period == 0 && (owner || (EXT && a.crit != 0))) {
+        // the paper's rule: a fresh tenure per move, drawn by the owner only
+        // (by every thread when the other criteria restamp touching pairs)
+        const uint32_t x = walk_draw(a.seed, wid, 1u, (uint32_t)(it - 1));
+        stamp = it + tmin + (int)below(x, (uint32_t)(tmax - tmin + 1));
+      }
+      if constexpr (EXT) {
+        if (a.crit != 0) {
+          // New marks of the pairs touching r or s, read through this
+          // move's own marks (units r, s leave locations pr, ps), which
+          // thread 0 also stores for the next iterations.
+          int32_t* loc_until = rule_tables();
+          int32_t* unit_until = loc_until + n * n;
+          const int pr = moved_from[0], ps = moved_from[1];
+          auto loc_mark = [&](int u, int l) {
+            return (u == r && l == pr) || (u == s && l == ps) ? stamp : loc_until[u * n + l];
+          };
+          auto unit_mark = [&](int u) { return u == r || u == s ? stamp : unit_until[u]; };
+          auto after = [&](int x) { return x == r ? ps : x == s ? pr : S.perm[x]; };
+          auto mark = [&](int u, int v) {
+            return a.crit == 1 ? min(loc_mark(u, after(v)), loc_mark(v, after(u)))
+                               : max(unit_mark(u), unit_mark(v));
+          };
+          if (su == r || su == s) {
+            for (int i = 0; i < slen; ++i) S.tabu[i * NT + tid] = mark(su, sv + i);
+          } else {
+            if (r >= sv && r < sv + slen) S.tabu[(r - sv) * NT + tid] = mark(su, r);
+            if (s >= sv && s < sv + slen) S.tabu[(s - sv) * NT + tid] = mark(su, s);
+          }
+          if (tid == 0) {
+            loc_until[r * n + pr] = stamp;
+            loc_until[s * n + ps] = stamp;
+            unit_until[r] = stamp;
+            unit_until[s] = stamp;
+          }
+        }
+        // read above by every thread before the barrier
+        if (a.lambda != 0 && owner) applied()[r * n + s] += 1;
+      }
+      update_and_scan(ext, r, s, true, it + 1, stamp, cur, best, bd, bk);
+      if (fq && owner) atomicAdd(fq + s * a.p_stride + r, 1);
+      swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
+      DT* t = gc; gc = gn; gn = t;
     }
-    if (bk == kNoMove) {
-      status = 1;
-      break;
-    }
-    const int r = (int)(bk >> 8), s = (int)(bk & 0xffu);
-    cur += bd;
-    done = it;
-    if (warp0) h = fnv_step(h, r, s);
-    if (cur < best) {
-      best = cur;
-      best_iter = it;
-      copy_pending = true;
-    }
-    if (period > 0 && --tleft == 0) {  // it = 1, period + 1, ...
-      const uint32_t x = walk_draw(a.seed, wid, 1u, tdraw++);
-      tenure = tmin + (int)below(x, (uint32_t)(tmax - tmin + 1));
-      tleft = period;
-    }
-    phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
-    __syncthreads();
-    int stamp = it + tenure;
-    if (period == 0 && su == r && s >= sv && s < sv + slen) {
-      // the paper's rule: a fresh tenure per move, drawn by the owner only
-      const uint32_t x = walk_draw(a.seed, wid, 1u, (uint32_t)(it - 1));
-      stamp = it + tmin + (int)below(x, (uint32_t)(tmax - tmin + 1));
-    }
-    update_and_scan(r, s, true, it + 1, stamp, cur, best, bd, bk);
-    if (fq && su == r && s >= sv && s < sv + slen) atomicAdd(fq + s * a.p_stride + r, 1);
-    swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
-    DT* t = gc; gc = gn; gn = t;
-  }
+  };
+  if (rules)
+    tabu_loop(std::true_type{});
+  else
+    tabu_loop(std::false_type{});
   __syncthreads();
   if (copy_pending)
     for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];

@@ -145,7 +145,7 @@ qap_status place(qap_server* sv, Request* r) {
   QAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->fn, r->plan.nt, r->smem));
   if (occ < 1) return QAP_EUNSUPPORTED;
   r->grid = std::min(W, occ * sv->sms);
-  r->ws_stride = workspace_per_cta(r->plan, r->dbytes);
+  r->ws_stride = workspace_per_cta(r->plan, r->dbytes, n, &r->params);
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -198,6 +198,7 @@ qap_status launch(qap_server* sv, Request* r) {
                      reinterpret_cast<const int8_t*>(dev + r->offD), r->plan.nt, r->fbytes);
   const qap_walk_outputs d = carve_outputs(reinterpret_cast<char*>(dev + r->offOut), OL, W);
   a.s = make_search_args(&r->params, &d, n);
+  a.s.rws_off = delta_workspace(r->plan, r->dbytes);
   a.walks = W;
   a.walk_offset = 0;
   a.starts = nullptr;
@@ -326,7 +327,9 @@ qap_status qap_server_submit(qap_server* sv, const int64_t* F, const int64_t* D,
   auto r = std::unique_ptr<Request>(new (std::nothrow) Request());
   if (!r) return QAP_ENOMEM;
   QAP_TRY(inspect_instance(F, D, n, &r->di));
-  r->dbytes = ((flags & QAP_FORCE_INT64) || r->di.bound > (int64_t)INT_MAX - 1) ? 8 : 4;
+  // int64 deltas when B, or B plus the largest frequency penalty, needs them
+  r->dbytes = ((flags & QAP_FORCE_INT64) || r->di.bound > (int64_t)INT_MAX - 1 ||
+               check_penalty(params, 4, r->di.bound) != QAP_OK) ? 8 : 4;
   r->fbytes = (r->di.maxF <= 127 && r->dbytes == 4) ? 1 : 2;
   r->di.ldF = pad_ldF(n, r->fbytes);
   r->di.ldP = pad_ldP(n);

@@ -57,3 +57,16 @@ def test_noalloc_rejects_sizes_beyond_its_limit(torch):
         stream.synchronize()
         assert e.value.status == q.EINVAL
         assert "static scratch limit" in q.last_error()
+
+
+def test_noalloc_rejects_rules_that_need_a_workspace(torch):
+    with _batch() as b:
+        outs = b.device_outputs(2)
+        stream = torch.cuda.Stream()
+        for kw in [dict(criterion=q.TABU_UNIT), dict(freq_penalty=3)]:
+            prm = q.make_params(2, seed=1, iters=10, tenure=(1, 2, 0), **kw)
+            with pytest.raises(q.QapError) as e:
+                q.qap_batch_search_noalloc(b.h, prm, {k: v.data_ptr() for k, v in outs.items()},
+                                           b.p_stride, stream.cuda_stream)
+            assert e.value.status == q.EUNSUPPORTED
+        stream.synchronize()
