@@ -179,8 +179,7 @@ qap_status qap_create(const int64_t* F, const int64_t* D, int32_t n, uint32_t fl
     return s;
   };
   c->dbytes = ((flags & QAP_FORCE_INT64) || di.bound > (int64_t)INT_MAX - 1) ? 8 : 4;
-  // int8 flows (dp4a rows) when they fit and deltas are int32; else int16
-  c->fbytes = (di.maxF <= 127 && c->dbytes == 4) ? 1 : 2;
+  c->fbytes = flow_bytes(di, c->dbytes);
   di.ldF = pad_ldF(n, c->fbytes);
   di.ldP = pad_ldP(n);
   c->di = di;
@@ -388,17 +387,20 @@ qap_status qap_batch_create(int32_t count, const int64_t* const* F, const int64_
   };
   b->count = count;
   b->di.resize(count);
-  int64_t maxF = 0, maxB = 0;
+  int64_t maxB = 0;
+  int bytevec = 1;
   for (int i = 0; i < count; ++i) {
     qap_status st = inspect_instance(F[i], D[i], n[i], &b->di[i]);
     if (st != QAP_OK) return fail(st);
-    maxF = std::max(maxF, b->di[i].maxF);
+    bytevec &= b->di[i].bytevec;
     maxB = std::max(maxB, b->di[i].bound);
     b->nmax = std::max(b->nmax, n[i]);
   }
   // one delta width and one flow width for the whole batch
   b->dbytes = ((flags & QAP_FORCE_INT64) || maxB > (int64_t)INT_MAX - 1) ? 8 : 4;
-  b->fbytes = (maxF <= 127 && b->dbytes == 4) ? 1 : 2;
+  DevInstance all;
+  all.bytevec = bytevec;
+  b->fbytes = flow_bytes(all, b->dbytes);
   qap_status st = device_attrs(&b->device, &b->sms, &b->smem_optin);
   if (st != QAP_OK) return fail(st);
   std::vector<unsigned char> blob;

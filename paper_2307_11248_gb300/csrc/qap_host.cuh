@@ -106,7 +106,14 @@ struct DevInstance {
   int n = 0, ldF = 0, ldP = 0, symF = 0, symD = 0;
   int64_t bound = 0;
   int64_t maxF = 0;
+  int bytevec = 0;  // every difference of two F entries, and of two D entries, fits int8
 };
+
+// int8 flows (dp4a rows, and byte vectors for the O(1) update) when the
+// instance allows them and the deltas are int32; else int16 flows.
+inline int flow_bytes(const DevInstance& di, int dbytes) {
+  return (di.bytevec && dbytes == 4) ? 1 : 2;
+}
 
 inline int pad_ldF(int n, int fbytes) { return (16 / fbytes) * (((n * fbytes + 15) / 16) | 1); }
 inline int pad_ldP(int n) { return 16 * (((n + 15) / 16) | 1); }
@@ -116,6 +123,7 @@ inline qap_status inspect_instance(const int64_t* F, const int64_t* D, int n, De
   if (!F || !D || n < 2) return QAP_EINVAL;
   if (n > kMaxN) return QAP_EUNSUPPORTED;
   int64_t mF = 0, mD = 0;
+  int64_t loF = F[0], hiF = F[0], loD = D[0], hiD = D[0];
   int symF = 1, symD = 1;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
@@ -123,6 +131,10 @@ inline qap_status inspect_instance(const int64_t* F, const int64_t* D, int n, De
       if (f < INT16_MIN || f > INT16_MAX || d < INT8_MIN || d > INT8_MAX) return QAP_EUNSUPPORTED;
       mF = std::max<int64_t>(mF, f < 0 ? -f : f);
       mD = std::max<int64_t>(mD, d < 0 ? -d : d);
+      loF = std::min(loF, f);
+      hiF = std::max(hiF, f);
+      loD = std::min(loD, d);
+      hiD = std::max(hiD, d);
       if (f != F[(size_t)j * n + i]) symF = 0;
       if (d != D[(size_t)j * n + i]) symD = 0;
     }
@@ -132,6 +144,7 @@ inline qap_status inspect_instance(const int64_t* F, const int64_t* D, int n, De
   di->symD = symD;
   di->bound = (nn * nn + 8 * nn + 32) * mF * mD;  // < 2^40 for n <= 181
   di->maxF = mF;
+  di->bytevec = mF <= 127 && hiF - loF <= 127 && hiD - loD <= 127;
   return QAP_OK;
 }
 

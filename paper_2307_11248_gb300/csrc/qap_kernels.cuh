@@ -156,6 +156,9 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int ldF, int fbytes, in
 template <typename DT> struct DeltaMax;
 template <> struct DeltaMax<int32_t> { static constexpr int32_t v = INT_MAX; };
 template <> struct DeltaMax<int64_t> { static constexpr int64_t v = LLONG_MAX; };
+template <typename DT> struct DeltaMin;
+template <> struct DeltaMin<int32_t> { static constexpr int32_t v = INT_MIN; };
+template <> struct DeltaMin<int64_t> { static constexpr int64_t v = LLONG_MIN; };
 
 // ---------------------------------------------------------------------------
 // row chunks: F rows as int8 (16 per chunk, dp4a) or int16 (8, dp2a)
@@ -192,30 +195,44 @@ template <> struct Chunk<int16_t> {
 // ---------------------------------------------------------------------------
 template <typename FE> struct VecOps;
 
+// The O(1) update of a pair (u, v) disjoint from the move,
+//   d + (a_u - a_v)(b_u - b_v) + (c_u - c_v)(e_u - e_v),
+// from the per-index vectors (a, b, c, e) that phase X writes.
+//
+// int8 flows: the host admits them only when every difference of two F
+// entries and of two D entries fits a byte, so a, b, c, e are bytes.
+// Expanding the products, the update is w_u + w_v - (a_u b_v + c_u e_v +
+// b_u a_v + e_u c_v) with w_x = a_x b_x + c_x e_x: one dp4a of the bytes
+// (a_u, c_u, b_u, e_u) with (b_v, e_v, a_v, c_v).  Index x stores the
+// second form and w_x; the owner of row u permutes its own bytes once.
 template <> struct VecOps<int8_t> {
-  using V = int2;
+  using V = int2;                  // (bytes b, e, a, c; w)
+  struct U { int A, w; };          // (bytes a, c, b, e; w) of the row index u
   __device__ __forceinline__ static V pack(int a, int b, int c, int e) {
-    return make_int2((int)(((uint32_t)a & 0xffffu) | ((uint32_t)b << 16)),
-                     (int)(((uint32_t)c & 0xffffu) | ((uint32_t)e << 16)));
+    const uint32_t x = ((uint32_t)b & 0xffu) | (((uint32_t)e & 0xffu) << 8) |
+                       (((uint32_t)a & 0xffu) << 16) | ((uint32_t)c << 24);
+    return make_int2((int)x, a * b + c * e);
   }
-  __device__ __forceinline__ static void unpack(const V w, int& a, int& b, int& c, int& e) {
-    a = (int)(short)(w.x & 0xffff);
-    b = w.x >> 16;
-    c = (int)(short)(w.y & 0xffff);
-    e = w.y >> 16;
+  __device__ __forceinline__ static U prep(const V u) {
+    return U{(int)__byte_perm((uint32_t)u.x, 0u, 0x1032u), u.y};
+  }
+  template <typename DT>
+  __device__ __forceinline__ static DT update(const U& u, const V v, DT d) {
+    // wrap-around sums: only the final value is bounded
+    return (DT)((uint32_t)d + (uint32_t)u.w + (uint32_t)v.y - (uint32_t)__dp4a(u.A, v.x, 0));
   }
 };
 
 template <> struct VecOps<int16_t> {
-  using V = int4;
+  using V = int4;                  // (a, b, c, e)
+  using U = int4;
   __device__ __forceinline__ static V pack(int a, int b, int c, int e) {
     return make_int4(a, b, c, e);
   }
-  __device__ __forceinline__ static void unpack(const V w, int& a, int& b, int& c, int& e) {
-    a = w.x;
-    b = w.y;
-    c = w.z;
-    e = w.w;
+  __device__ __forceinline__ static U prep(const V u) { return u; }
+  template <typename DT>
+  __device__ __forceinline__ static DT update(const U& u, const V v, DT d) {
+    return d + (DT)((u.x - v.x) * (u.y - v.y) + (u.z - v.z) * (u.w - v.w));
   }
 };
 
@@ -708,7 +725,11 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
 
   // Owners' pass after move (r, s): new deltas, then the scan for the next
   // iteration `nit` (tabu phase) or the next descent step.  Branch-free per
-  // slot so the shared-memory loads of all slots are in flight together.
+  // slot so the shared-memory loads of all slots are in flight together:
+  // every slot takes the O(1) update, except the pairs (su, r) and (su, s)
+  // of rows other than r and s, which take their recomputed rows.  The few
+  // threads holding segments of rows r and s then recompute those and scan
+  // again.
   // Tables of the other tabu criteria and of the frequency penalty, in the
   // CTA's workspace: loc_until[unit][location] (n x n), unit_until[unit] (n)
   // and applied[r][s] (n x n, the penalty's counts, row-major so that a
@@ -726,12 +747,32 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     const int32_t* crow = EXT ? applied() + su * n : nullptr;
     using VO = VecOps<FE>;
     const auto* vec = reinterpret_cast<const typename VO::V*>(S.vec);
+    const typename VO::U uu = VO::prep(vec[su]);
     const DT gr = gn[r], gs = gn[s];
     const bool tu = (su == r) | (su == s);        // every pair of the segment touches
-    const int ubase = su == r ? 0 : n;
-    const DT gu = su == r ? gr : gs;
-    int ua, ub, uc, ue;
-    VO::unpack(vec[su], ua, ub, uc, ue);
+    const int ir = r - sv, is = s - sv;           // slots of (su, r), (su, s) if held
+    const DT xr = S.R[su] - gr, xs = S.R[n + su] - gs;
+    // admissible: not tabu (mark <= nit), or aspiring (ncur + d < nbest,
+    // i.e. d < nbest - ncur, clamped where no delta can reach it)
+    const int tlim = tabu ? nit : INT_MAX;
+    DT lim = DeltaMin<DT>::v;
+    if (!tabu) {
+      lim = DeltaMax<DT>::v;
+    } else if (a.aspiration) {
+      const int64_t l = (int64_t)nbest - (int64_t)ncur;
+      lim = l < (int64_t)DeltaMin<DT>::v ? DeltaMin<DT>::v : (DT)l;
+    }
+    auto rank = [&](DT d, int v) -> DT {
+      if constexpr (EXT) return d >= 0 ? d + (DT)a.lambda * (DT)crow[v] : d;
+      return d;
+    };
+    // the pair (r, s) itself only changes sign
+    DT nrs = 0;
+    if (su == r) {
+#pragma unroll
+      for (int i = 0; i < MAXPT; ++i)
+        if (i == is) nrs = -dl.get(i);
+    }
     bd = DeltaMax<DT>::v;
     bk = kNoMove;
 #pragma unroll
@@ -739,28 +780,36 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       if (i >= wlen) break;
       const bool valid = i < slen;
       const int v = valid ? sv + i : sv;
-      int va, vb, vc, ve;
-      VO::unpack(vec[v], va, vb, vc, ve);
-      const bool tvr = v == r, tv = tvr | (v == s);
-      const int idx = tu ? ubase + v : (tvr ? 0 : n) + su;  // in range for any v, su
-      const DT rv = S.R[idx];
-      const int tbl = S.tabu[i * NT + tid];
-      const DT gx = tu ? gu : (tvr ? gr : gs);
-      DT d = dl.get(i);
-      const DT o1 = d + (DT)((ua - va) * (ub - vb) + (uc - vc) * (ue - ve));
-      const bool isrs = (su == r) & (v == s);
-      d = isrs ? -d : (tu | tv) ? rv - gx : o1;
-      d = valid ? d : DeltaMax<DT>::v;
+      DT d = VO::update(uu, vec[v], dl.get(i));
+      d = i == ir ? xr : i == is ? xs : d;
       dl.set(i, d);
-      // the pair just applied carries its new stamp; the store follows the
-      // loop so no shared-memory store sits between the slots' loads
-      const int tb = isrs ? stamp : tbl;
-      const bool adm = !tabu || tb <= nit || (a.aspiration && ncur + d < nbest);
-      DT sc = d;
-      if constexpr (EXT) sc = d >= 0 ? d + (DT)a.lambda * (DT)crow[v] : d;
-      if (valid && adm && sc < bd) {
+      const int tb = S.tabu[i * NT + tid];
+      const DT sc = rank(d, v);
+      if (valid && (tb <= tlim || d < lim) && sc < bd) {
         bd = sc;
         bk = ukey | (uint32_t)v;
+      }
+    }
+    if (tu) {
+      // rows r and s: every pair recomputed, then scanned again; the pair
+      // just applied carries its new mark
+      const int ubase = su == r ? 0 : n;
+      const DT gu = su == r ? gr : gs;
+      bd = DeltaMax<DT>::v;
+      bk = kNoMove;
+#pragma unroll
+      for (int i = 0; i < MAXPT; ++i) {
+        if (i >= slen) break;
+        const int v = sv + i;
+        const bool isrs = (su == r) & (i == is);
+        const DT d = isrs ? nrs : S.R[ubase + v] - gu;
+        dl.set(i, d);
+        const int tb = isrs ? stamp : S.tabu[i * NT + tid];
+        const DT sc = rank(d, v);
+        if ((tb <= tlim || d < lim) && sc < bd) {
+          bd = sc;
+          bk = ukey | (uint32_t)v;
+        }
       }
     }
     if (tabu && su == r && s >= sv && s < sv + slen) S.tabu[(s - sv) * NT + tid] = stamp;

@@ -330,7 +330,7 @@ qap_status qap_server_submit(qap_server* sv, const int64_t* F, const int64_t* D,
   // int64 deltas when B, or B plus the largest frequency penalty, needs them
   r->dbytes = ((flags & QAP_FORCE_INT64) || r->di.bound > (int64_t)INT_MAX - 1 ||
                check_penalty(params, 4, r->di.bound) != QAP_OK) ? 8 : 4;
-  r->fbytes = (r->di.maxF <= 127 && r->dbytes == 4) ? 1 : 2;
+  r->fbytes = flow_bytes(r->di, r->dbytes);
   r->di.ldF = pad_ldF(n, r->fbytes);
   r->di.ldP = pad_ldP(n);
   r->params = *params;
