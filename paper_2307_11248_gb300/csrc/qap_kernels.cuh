@@ -288,9 +288,6 @@ __device__ __forceinline__ uint64_t fnv_step(uint64_t h, uint32_t r, uint32_t s)
   return (h ^ (uint64_t)((r << 16) | s)) * 1099511628211ull;
 }
 
-__device__ __forceinline__ unsigned group_mask(int G) {
-  return (G == 32 ? kFull : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
-}
 
 // ---------------------------------------------------------------------------
 // per-walk state views
@@ -352,8 +349,8 @@ __device__ __forceinline__ void compute_g(const WalkSmem<DT, FE>& S, DT* g, int 
   const int grp = threadIdx.x / G;
   const int NG = NT / G;
   const int nc = (n + C::W - 1) / C::W;
-  const unsigned gmask = group_mask(G);
-  for (int k = grp; k < n; k += NG) {
+  for (int base = 0; base < n; base += NG) {  // whole CTA per round (runs once per walk)
+    const int k = min(base + grp, n - 1);
     const auto* Fk = reinterpret_cast<const typename C::FV*>(S.F + k * ldF);
     const auto* Pk = reinterpret_cast<const typename C::QV*>(S.P + k * ldP);
     const auto* Ftk = reinterpret_cast<const typename C::FV*>(S.Ft + k * ldF);
@@ -363,8 +360,8 @@ __device__ __forceinline__ void compute_g(const WalkSmem<DT, FE>& S, DT* g, int 
       acc = C::dot(Fk[c], Pk[c], acc);
       if (!sym) acc = C::dot(Ftk[c], Ptk[c], acc);
     }
-    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o);
-    if (lg == 0) g[k] = sym ? (DT)2 * (DT)acc : (DT)acc;
+    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (lg == 0 && base + grp < n) g[k] = sym ? (DT)2 * (DT)acc : (DT)acc;
   }
 }
 
@@ -385,7 +382,6 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
   const int grp = threadIdx.x / G;
   const int NG = NT / G;
   const int nc = (n + C::W - 1) / C::W;
-  const unsigned gmask = group_mask(G);
   const FE* F = S.F;
   const int8_t* Q = S.P;
   const FE* Ft = S.Ft;
@@ -398,12 +394,39 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
   const QV* Qs = reinterpret_cast<const QV*>(Q + s * ldP);
   const QV* Qtr = reinterpret_cast<const QV*>(Qt + r * ldP);
   const QV* Qts = reinterpret_cast<const QV*>(Qt + s * ldP);
-  for (int k = grp; k < n; k += NG) {
+  // 2x2 blocks of F and Q at {r, s}
+  const int fRR = F[r * ldF + r], fRS = F[r * ldF + s];
+  const int fSR = F[s * ldF + r], fSS = F[s * ldF + s];
+  const int qRR = Q[r * ldP + r], qRS = Q[r * ldP + s];
+  const int qSR = Q[s * ldP + r], qSS = Q[s * ldP + s];
+  // Up to 512 threads the bound is the same for every lane of a warp (its
+  // first group), so whole warps run each round and the reductions use
+  // full-warp shuffles; lanes past n work on row n - 1 and store nothing.
+  // At 1024 threads (measured faster) each group runs its own rounds and
+  // shuffles within the group.
+  constexpr bool kWarpRounds = NT < 1024;
+  const int nb = kWarpRounds ? n - (threadIdx.x & ~31) / G : n - grp;
+  const unsigned smask =
+      kWarpRounds ? kFull : ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+  for (int base = 0; base < nb; base += NG) {
+    const int k0 = base + grp;
+    const int k = min(k0, n - 1);
     const bool gt = (k == r) | (k == s);
     // k-task: Ar = F[r].Q[k] + F^T[r].Q^T[k]   Br = F[k].Q[s] + F^T[k].Q^T[s]
     //         As = F[s].Q[k] + F^T[s].Q^T[k]   Bs = F[k].Q[r] + F^T[k].Q^T[r]
     // g-task k = r: Ar with the row s in place of k; k = s: As with row r
     const int kq = gt ? (k == r ? s : r) : k;
+    // scalars of the finish; loaded before the dots so their latency hides
+    // under them, except at 1024 threads, whose 64 registers cannot hold them
+    struct Fin { int Frk, Fsk, Fkr, Fks, Qrk, Qsk, Qkr, Qks, Fkk, Qkk; DT gck; };
+    auto load_fin = [&]() {
+      return Fin{F[r * ldF + k],  F[s * ldF + k],  Ft[r * ldF + k], Ft[s * ldF + k],
+                 Q[r * ldP + k],  Q[s * ldP + k],  Qt[r * ldP + k], Qt[s * ldP + k],
+                 F[k * ldF + k],  Q[k * ldP + k],  gc[k]};
+    };
+    constexpr bool kEarly = NT < 1024;
+    Fin fin{};
+    if constexpr (kEarly) fin = load_fin();
     const FV* Fk = reinterpret_cast<const FV*>(F + kq * ldF);
     const FV* Ftk = reinterpret_cast<const FV*>(Ft + kq * ldF);
     const QV* Qk = reinterpret_cast<const QV*>(Q + kq * ldP);
@@ -436,19 +459,14 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
     const bool odd = lg & 1;
     int A = odd ? As : Ar, B = odd ? Bs : Br;
     if (G > 1) {
-      A += __shfl_xor_sync(gmask, odd ? Ar : As, 1);
-      B += __shfl_xor_sync(gmask, odd ? Br : Bs, 1);
+      A += __shfl_xor_sync(smask, odd ? Ar : As, 1);
+      B += __shfl_xor_sync(smask, odd ? Br : Bs, 1);
       for (int o = 2; o < G; o <<= 1) {
-        A += __shfl_xor_sync(gmask, A, o);
-        B += __shfl_xor_sync(gmask, B, o);
+        A += __shfl_xor_sync(smask, A, o);
+        B += __shfl_xor_sync(smask, B, o);
       }
     }
-    if (lg > 1) continue;
-    // 2x2 blocks of F and Q at {r, s}
-    const int fRR = F[r * ldF + r], fRS = F[r * ldF + s];
-    const int fSR = F[s * ldF + r], fSS = F[s * ldF + s];
-    const int qRR = Q[r * ldP + r], qRS = Q[r * ldP + s];
-    const int qSR = Q[s * ldP + r], qSS = Q[s * ldP + s];
+    if (k0 >= n || lg > 1) continue;
     if (gt) {
       // g'[x] = A + (F[x][r]-F[x][s])(Q[xb][s]-Q[xb][r])
       //           + (F[r][x]-F[s][x])(Q[s][xb]-Q[r][xb])
@@ -460,13 +478,12 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
       gn[k] = sym ? (DT)2 * ((DT)A0 + (DT)c1) : (DT)A0 + (DT)c1 + (DT)c2;
       continue;
     }
-    const int Frk = F[r * ldF + k], Fsk = F[s * ldF + k];
-    const int Fkr = Ft[r * ldF + k], Fks = Ft[s * ldF + k];
-    const int Qrk = Q[r * ldP + k], Qsk = Q[s * ldP + k];
-    const int Qkr = Qt[r * ldP + k], Qks = Qt[s * ldP + k];
-    const int Fkk = F[k * ldF + k], Qkk = Q[k * ldP + k];
+    if constexpr (!kEarly) fin = load_fin();
+    const int Frk = fin.Frk, Fsk = fin.Fsk, Fkr = fin.Fkr, Fks = fin.Fks;
+    const int Qrk = fin.Qrk, Qsk = fin.Qsk, Qkr = fin.Qkr, Qks = fin.Qks;
+    const int Fkk = fin.Fkk, Qkk = fin.Qkk;
     const int a = Frk - Fsk, b = Qrk - Qsk, c = Fkr - Fks, e = Qkr - Qks;
-    const DT gk = gc[k] - (DT)(a * b) - (DT)(c * e);
+    const DT gk = fin.gck - (DT)(a * b) - (DT)(c * e);
     for (int xi = lg; xi < 2; xi += (G == 1 ? 1 : 2)) {
       const bool xs = xi != 0;
       const int fxx = xs ? fSS : fRR;   // F[x][x]
@@ -710,6 +727,10 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   c0 = block_sum<NT>(c0, S.sum);
   compute_g<DT, FE, NT>(S, S.g0, n, ldF, ldP, sym, G);
   DeltaSlots<DT, NT, MAXPT, (STORE & kGlobalDelta) != 0> dl(ws);
+  // owner pass form: the O(1) update everywhere, then the rows r and s
+  // apart (register slots), or one pass choosing per slot (workspace slots,
+  // read and written once)
+  constexpr bool kSplitPass = !(STORE & kGlobalDelta);
 #pragma unroll
   for (int i = 0; i < MAXPT; ++i) {
     dl.set(i, i < slen ? delta_serial<DT, FE>(S, n, ldF, ldP, sym, su, sv + i)
@@ -766,47 +787,76 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       if constexpr (EXT) return d >= 0 ? d + (DT)a.lambda * (DT)crow[v] : d;
       return d;
     };
-    // the pair (r, s) itself only changes sign
-    DT nrs = 0;
-    if (su == r) {
-#pragma unroll
-      for (int i = 0; i < MAXPT; ++i)
-        if (i == is) nrs = -dl.get(i);
-    }
     bd = DeltaMax<DT>::v;
     bk = kNoMove;
+    if constexpr (kSplitPass) {
+      // the pair (r, s) itself only changes sign
+      DT nrs = 0;
+      if (su == r) {
 #pragma unroll
-    for (int i = 0; i < MAXPT; ++i) {
-      if (i >= wlen) break;
-      const bool valid = i < slen;
-      const int v = valid ? sv + i : sv;
-      DT d = VO::update(uu, vec[v], dl.get(i));
-      d = i == ir ? xr : i == is ? xs : d;
-      dl.set(i, d);
-      const int tb = S.tabu[i * NT + tid];
-      const DT sc = rank(d, v);
-      if (valid && (tb <= tlim || d < lim) && sc < bd) {
-        bd = sc;
-        bk = ukey | (uint32_t)v;
+        for (int i = 0; i < MAXPT; ++i)
+          if (i == is) nrs = -dl.get(i);
       }
-    }
-    if (tu) {
-      // rows r and s: every pair recomputed, then scanned again; the pair
-      // just applied carries its new mark
-      const int ubase = su == r ? 0 : n;
-      const DT gu = su == r ? gr : gs;
-      bd = DeltaMax<DT>::v;
-      bk = kNoMove;
 #pragma unroll
       for (int i = 0; i < MAXPT; ++i) {
-        if (i >= slen) break;
-        const int v = sv + i;
-        const bool isrs = (su == r) & (i == is);
-        const DT d = isrs ? nrs : S.R[ubase + v] - gu;
+        if (i >= wlen) break;
+        const bool valid = i < slen;
+        const int v = valid ? sv + i : sv;
+        DT d = VO::update(uu, vec[v], dl.get(i));
+        d = i == ir ? xr : i == is ? xs : d;
         dl.set(i, d);
-        const int tb = isrs ? stamp : S.tabu[i * NT + tid];
+        const int tb = S.tabu[i * NT + tid];
         const DT sc = rank(d, v);
-        if ((tb <= tlim || d < lim) && sc < bd) {
+        if (valid && (tb <= tlim || d < lim) && sc < bd) {
+          bd = sc;
+          bk = ukey | (uint32_t)v;
+        }
+      }
+      if (tu) {
+        // rows r and s: every pair recomputed, then scanned again; the pair
+        // just applied carries its new mark
+        const int ubase = su == r ? 0 : n;
+        const DT gu = su == r ? gr : gs;
+        bd = DeltaMax<DT>::v;
+        bk = kNoMove;
+#pragma unroll
+        for (int i = 0; i < MAXPT; ++i) {
+          if (i >= slen) break;
+          const int v = sv + i;
+          const bool isrs = (su == r) & (i == is);
+          const DT d = isrs ? nrs : S.R[ubase + v] - gu;
+          dl.set(i, d);
+          const int tb = isrs ? stamp : S.tabu[i * NT + tid];
+          const DT sc = rank(d, v);
+          if ((tb <= tlim || d < lim) && sc < bd) {
+            bd = sc;
+            bk = ukey | (uint32_t)v;
+          }
+        }
+      }
+    } else {
+      // one pass, each slot choosing between its update and its recomputed
+      // row
+      const int ubase = su == r ? 0 : n;
+      const DT gu = su == r ? gr : gs;
+#pragma unroll
+      for (int i = 0; i < MAXPT; ++i) {
+        if (i >= wlen) break;
+        const bool valid = i < slen;
+        const int v = valid ? sv + i : sv;
+        const bool tvr = i == ir, tv = tvr | (i == is);
+        const int idx = tu ? ubase + v : (tvr ? 0 : n) + su;  // in range for any v, su
+        const DT rv = S.R[idx];
+        const int tbl = S.tabu[i * NT + tid];
+        const DT gx = tu ? gu : (tvr ? gr : gs);
+        DT d = dl.get(i);
+        const DT o1 = VO::update(uu, vec[v], d);
+        const bool isrs = (su == r) & (i == is);
+        d = isrs ? -d : (tu | tv) ? rv - gx : o1;
+        dl.set(i, d);
+        const int tb = isrs ? stamp : tbl;
+        const DT sc = rank(d, v);
+        if (valid && (tb <= tlim || d < lim) && sc < bd) {
           bd = sc;
           bk = ukey | (uint32_t)v;
         }
