@@ -241,6 +241,8 @@ typedef struct {
   int32_t grid;              /* CTAs of the persistent launch             */
   int32_t ctas_per_sm;
   int32_t sms;
+  int32_t classes;           /* launches of a batch search (size classes);
+                                1 for one instance                          */
 } qap_plan_info;
 qap_status qap_plan(qap_ctx* ctx, const qap_search_params* params, qap_plan_info* out);
 
@@ -283,7 +285,11 @@ void qap_batch_destroy(qap_batch* b);
 qap_status qap_batch_info(const qap_batch* b, int32_t* count, int32_t* nmax,
                           int32_t* delta_bytes);
 
-/* Launch shape of a batch search (one plan for the largest n). */
+/* Launch shape of a batch search.  Each instance takes the plan its own n
+ * would get alone; instances with the same plan form a size class with one
+ * persistent launch, and the classes run concurrently on internal streams
+ * forked from and joined back into the caller's stream.  Reports the class
+ * of the largest n and the number of classes. */
 qap_status qap_batch_plan(qap_batch* b, const qap_search_params* params, qap_plan_info* out);
 
 /* Run params->starts walks of every instance.  Output row i * starts + k
@@ -291,10 +297,12 @@ qap_status qap_batch_plan(qap_batch* b, const qap_search_params* params, qap_pla
  * (the first n[i] are the permutation).  params->launch must be
  * QAP_LAUNCH_PERSISTENT.
  * qap_batch_search: host outputs, blocking.
- * qap_batch_search_async: device outputs, stream-ordered (a counter reset
- *   and one kernel launch).  The first call for a given (starts, thread
- *   count) writes device tables synchronously and must not be captured in
- *   a CUDA graph; later calls can be.
+ * qap_batch_search_async: device outputs, stream-ordered (per size class a
+ *   counter reset and one kernel launch, on internal streams forked from
+ *   `stream` by an event and joined back into it).  The first call for a
+ *   given (starts, thread count, rule tables on or off) writes device
+ *   tables synchronously and must not be captured in a CUDA graph; later
+ *   calls can be.
  * Errors: QAP_EINVAL, QAP_EUNSUPPORTED, QAP_ENOMEM, QAP_ECUDA. */
 qap_status qap_batch_search(qap_batch* b, const qap_search_params* params,
                             const qap_walk_outputs* out, int32_t p_stride);

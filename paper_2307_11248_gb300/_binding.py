@@ -75,7 +75,7 @@ class ServerStats(ctypes.Structure):
 class PlanInfo(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in
                 ("threads_per_walk", "pairs_per_thread", "smem_bytes", "grid", "ctas_per_sm",
-                 "sms")]
+                 "sms", "classes")]
 
 
 OUTPUT_FIELDS = {  # name -> (dtype, per-walk shape multiplier uses n)

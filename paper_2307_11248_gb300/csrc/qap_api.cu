@@ -41,6 +41,18 @@ struct qap_ctx {
   size_t ws_bytes = 0;
 };
 
+// Instances of a batch that share one launch plan (a size class).
+struct BatchClass {
+  Plan plan;
+  const void* fn = nullptr;
+  int smem = 0, grid = 0, ctas_per_sm = 0;
+  std::vector<int> members;  // instance indices, largest n first
+  int item_off = 0, items = 0;
+  size_t ws_off = 0, ws_stride = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
 struct qap_batch {
   int device = 0, sms = 0, smem_optin = 0;
   int count = 0, nmax = 0;
@@ -48,19 +60,24 @@ struct qap_batch {
   std::vector<DevInstance> di;
   std::vector<size_t> offF, offFt, offD;
   void* data = nullptr;  // every instance's F, F^T and D
-  qapk::InstArgs* d_insts = nullptr;
-  int cached_nt = 0;     // plan the instance table was written for
-  int32_t* d_items = nullptr;  // item_inst | item_walk | row_base
-  int cached_walks = 0;
-  int* d_counter = nullptr;
+  qapk::InstArgs* d_insts = nullptr;  // one table per thread count (128..1024)
+  int insts_written = 0;              // bit t: the table for 128 << t is written
+  int* d_counter = nullptr;           // one work counter per class
   cudaStream_t stream = nullptr;
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
-  void* ws = nullptr;  // workspace of large-n plans
+  void* ws = nullptr;  // workspace of large-n plans and rule tables
   size_t ws_bytes = 0;
+  // size classes of the last search shape (threads_per_walk, starts)
+  std::vector<BatchClass> classes;
+  int classes_threads = -1, classes_walks = 0, classes_rules = -1;
+  int32_t* d_class_items = nullptr;  // per class item_inst | item_walk, then row_base
+  cudaEvent_t fork = nullptr;
 };
 
 namespace {
+
+constexpr int kCounterStride = 32;  // ints between the classes' work counters
 
 struct Launch {
   const void* fn;
@@ -102,43 +119,129 @@ qap_status plan_batch(qap_batch* b, const qap_search_params* p, Launch* L) {
   return occupancy(L, b->sms, b->count * p->starts);
 }
 
-// Writes the instance table for thread count nt and the item lists for W
-// walks per instance (longest instances first), synchronously; the results
-// are cached, so later calls with the same nt and W only launch.
-qap_status batch_tables(qap_batch* b, int nt, int W) {
-  if (b->cached_nt != nt) {
-    std::vector<qapk::InstArgs> h(b->count);
-    char* base = static_cast<char*>(b->data);
-    for (int i = 0; i < b->count; ++i)
-      h[i] = inst_args(b->di[i], base + b->offF[i], base + b->offFt[i],
-                       reinterpret_cast<int8_t*>(base + b->offD[i]), nt, b->fbytes);
-    QAP_CUDA(cudaMemcpy(b->d_insts, h.data(), sizeof(qapk::InstArgs) * b->count,
-                        cudaMemcpyHostToDevice));
-    b->cached_nt = nt;
+int nt_index(int nt) { return nt == 128 ? 0 : nt == 256 ? 1 : nt == 512 ? 2 : 3; }
+
+// Size classes of a batch search: every instance takes the plan its own n
+// would get alone, and instances with the same plan share one persistent
+// launch.  Classes run on side streams, largest n first, so the longest
+// walks start first and the other classes fill the SMs as those finish.
+// The instance tables (one per thread count) and the item lists are written
+// synchronously and cached for the same (threads, starts, rule tables).
+qap_status plan_classes(qap_batch* b, const qap_search_params* p) {
+  const int rules = uses_rule_tables(p) ? 1 : 0;
+  const int W = p->starts;
+  if (!b->classes.empty() && b->classes_threads == p->threads_per_walk &&
+      b->classes_walks == W && b->classes_rules == rules)
+    return QAP_OK;
+  if ((size_t)b->count * W > (size_t)INT_MAX / 2) return QAP_EINVAL;
+  b->classes_threads = -1;
+  std::vector<Plan> plan_of(b->count);
+  for (int i = 0; i < b->count; ++i)
+    // the batch kernel also holds one static int
+    if (!choose_plan_fit(b->di[i].n, p->threads_per_walk, &b->di[i], 1, b->fbytes, b->dbytes,
+                         b->smem_optin, 16, &plan_of[i]))
+      return QAP_EUNSUPPORTED;
+  std::vector<int> order(b->count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->di[x].n > b->di[y].n; });
+  // keep the old classes' streams and events for reuse
+  std::vector<BatchClass> old;
+  old.swap(b->classes);
+  auto same = [](const Plan& x, const Plan& y) {
+    return x.nt == y.nt && x.maxpt == y.maxpt && x.store == y.store;
+  };
+  for (int i : order) {  // classes appear in order of their largest n
+    BatchClass* c = nullptr;
+    for (BatchClass& k : b->classes)
+      if (same(k.plan, plan_of[i])) c = &k;
+    if (!c) {
+      b->classes.emplace_back();
+      c = &b->classes.back();
+      c->plan = plan_of[i];
+    }
+    c->members.push_back(i);
   }
-  if (b->cached_walks != W) {
-    const size_t items = (size_t)b->count * W;
-    if (items > (size_t)INT_MAX / 2) return QAP_EINVAL;
-    std::vector<int> order(b->count);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return b->di[x].n > b->di[y].n; });
-    std::vector<int32_t> h(items * 2 + b->count);
-    size_t k = 0;
-    for (int inst : order)
+  for (size_t k = 0; k < b->classes.size(); ++k) {
+    if (k < old.size()) {
+      b->classes[k].side = old[k].side;
+      b->classes[k].done = old[k].done;
+      old[k].side = nullptr;
+      old[k].done = nullptr;
+    }
+  }
+  for (BatchClass& c : old) {
+    if (c.side) {
+      cudaStreamSynchronize(c.side);
+      cudaStreamDestroy(c.side);
+    }
+    if (c.done) cudaEventDestroy(c.done);
+  }
+  int item_off = 0;
+  size_t ws_off = 0;
+  for (BatchClass& c : b->classes) {
+    std::vector<DevInstance> dm;
+    int nmax = 0;
+    for (int i : c.members) {
+      dm.push_back(b->di[i]);
+      nmax = std::max(nmax, b->di[i].n);
+    }
+    c.smem = plan_smem(c.plan, dm.data(), (int)dm.size(), b->fbytes, b->dbytes);
+    c.fn = reinterpret_cast<const void*>(pick_batch_kernel(b->dbytes, b->fbytes, c.plan));
+    if (!c.fn) return QAP_EUNSUPPORTED;
+    QAP_TRY(prepare_kernel(c.fn, c.smem));
+    int occ = 0;
+    QAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.fn, c.plan.nt, c.smem));
+    if (occ < 1) return QAP_EUNSUPPORTED;
+    c.items = (int)c.members.size() * W;
+    c.item_off = item_off;
+    item_off += c.items;
+    c.ctas_per_sm = occ;
+    c.grid = std::min(c.items, occ * b->sms);
+    c.ws_stride = workspace_per_cta(c.plan, b->dbytes, nmax, p);
+    c.ws_off = ws_off;
+    ws_off += (c.ws_stride * c.grid + 255) / 256 * 256;
+    if (b->classes.size() > 1) {
+      if (!c.side) QAP_CUDA(cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking));
+      if (!c.done) QAP_CUDA(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
+    }
+    // the instance table for this thread count
+    const int t = nt_index(c.plan.nt);
+    if (!(b->insts_written & (1 << t))) {
+      std::vector<qapk::InstArgs> h(b->count);
+      char* base = static_cast<char*>(b->data);
+      for (int i = 0; i < b->count; ++i)
+        h[i] = inst_args(b->di[i], base + b->offF[i], base + b->offFt[i],
+                         reinterpret_cast<int8_t*>(base + b->offD[i]), c.plan.nt, b->fbytes);
+      QAP_CUDA(cudaMemcpy(b->d_insts + (size_t)t * b->count, h.data(),
+                          sizeof(qapk::InstArgs) * b->count, cudaMemcpyHostToDevice));
+      b->insts_written |= 1 << t;
+    }
+  }
+  if (b->classes.size() > 1 && !b->fork)
+    QAP_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  // item lists: class after class, each longest instances first; row bases
+  const size_t total = (size_t)item_off;
+  std::vector<int32_t> h(total * 2 + b->count);
+  for (const BatchClass& c : b->classes) {
+    size_t k = c.item_off;
+    for (int inst : c.members)
       for (int w = 0; w < W; ++w, ++k) {
         h[k] = inst;
-        h[items + k] = w;
+        h[total + k] = w;
       }
-    for (int i = 0; i < b->count; ++i) h[2 * items + i] = i * W;
-    if (b->d_items) cudaFree(b->d_items);
-    b->d_items = nullptr;
-    b->cached_walks = 0;
-    if (cudaMalloc(&b->d_items, h.size() * sizeof(int32_t)) != cudaSuccess) return QAP_ENOMEM;
-    QAP_CUDA(cudaMemcpy(b->d_items, h.data(), h.size() * sizeof(int32_t),
-                        cudaMemcpyHostToDevice));
-    b->cached_walks = W;
   }
+  for (int i = 0; i < b->count; ++i) h[2 * total + i] = i * W;
+  if (b->d_class_items) cudaFree(b->d_class_items);
+  b->d_class_items = nullptr;
+  if (cudaMalloc(&b->d_class_items, h.size() * sizeof(int32_t)) != cudaSuccess)
+    return QAP_ENOMEM;
+  QAP_CUDA(cudaMemcpy(b->d_class_items, h.data(), h.size() * sizeof(int32_t),
+                      cudaMemcpyHostToDevice));
+  QAP_TRY(grow(&b->ws, &b->ws_bytes, ws_off));
+  b->classes_threads = p->threads_per_walk;
+  b->classes_walks = W;
+  b->classes_rules = rules;
   return QAP_OK;
 }
 
@@ -235,6 +338,7 @@ qap_status qap_plan(qap_ctx* ctx, const qap_search_params* params, qap_plan_info
   out->grid = params->launch == QAP_LAUNCH_PLAIN ? 1 : L.grid;
   out->ctas_per_sm = L.ctas_per_sm;
   out->sms = ctx->sms;
+  out->classes = 1;
   return QAP_OK;
 }
 
@@ -426,9 +530,9 @@ qap_status qap_batch_create(int32_t count, const int64_t* const* F, const int64_
   if (cudaMalloc(&b->data, blob.size()) != cudaSuccess) return fail(QAP_ENOMEM);
   cudaError_t e = cudaMemcpy(b->data, blob.data(), blob.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy"));
-  if (cudaMalloc(&b->d_insts, sizeof(qapk::InstArgs) * count) != cudaSuccess)
+  if (cudaMalloc(&b->d_insts, sizeof(qapk::InstArgs) * count * 4) != cudaSuccess)
     return fail(QAP_ENOMEM);
-  if (cudaMalloc(&b->d_counter, 256) != cudaSuccess) return fail(QAP_ENOMEM);
+  if (cudaMalloc(&b->d_counter, kCounterStride * 4 * 64) != cudaSuccess) return fail(QAP_ENOMEM);
   e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreateWithFlags"));
   *out = b;
@@ -440,10 +544,18 @@ void qap_batch_destroy(qap_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->data) cudaFree(b->data);
   if (b->d_insts) cudaFree(b->d_insts);
-  if (b->d_items) cudaFree(b->d_items);
   if (b->d_counter) cudaFree(b->d_counter);
   if (b->scratch) cudaFree(b->scratch);
   if (b->ws) cudaFree(b->ws);
+  if (b->d_class_items) cudaFree(b->d_class_items);
+  for (BatchClass& c : b->classes) {
+    if (c.side) {
+      cudaStreamSynchronize(c.side);
+      cudaStreamDestroy(c.side);
+    }
+    if (c.done) cudaEventDestroy(c.done);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -461,14 +573,15 @@ qap_status qap_batch_plan(qap_batch* b, const qap_search_params* params, qap_pla
   if (!b || !out) return QAP_EINVAL;
   QAP_TRY(validate_params(params));
   QAP_CUDA(cudaSetDevice(b->device));
-  Launch L;
-  QAP_TRY(plan_batch(b, params, &L));
-  out->threads_per_walk = L.plan.nt;
-  out->pairs_per_thread = L.plan.maxpt;
-  out->smem_bytes = L.smem;
-  out->grid = L.grid;
-  out->ctas_per_sm = L.ctas_per_sm;
+  QAP_TRY(plan_classes(b, params));
+  const BatchClass& c = b->classes.front();  // the class of the largest n
+  out->threads_per_walk = c.plan.nt;
+  out->pairs_per_thread = c.plan.maxpt;
+  out->smem_bytes = c.smem;
+  out->grid = c.grid;
+  out->ctas_per_sm = c.ctas_per_sm;
   out->sms = b->sms;
+  out->classes = (int32_t)b->classes.size();
   return QAP_OK;
 }
 
@@ -480,29 +593,35 @@ qap_status qap_batch_search_async(qap_batch* b, const qap_search_params* params,
   if (params->launch != QAP_LAUNCH_PERSISTENT) return QAP_EINVAL;
   for (const DevInstance& d : b->di) QAP_TRY(check_penalty(params, b->dbytes, d.bound));
   QAP_CUDA(cudaSetDevice(b->device));
-  Launch L;
-  QAP_TRY(plan_batch(b, params, &L));
-  QAP_TRY(batch_tables(b, L.plan.nt, params->starts));
+  QAP_TRY(plan_classes(b, params));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int items = b->count * params->starts;
-  qapk::BatchArgs a{};
-  a.insts = b->d_insts;
-  a.item_inst = b->d_items;
-  a.item_walk = b->d_items + items;
-  a.row_base = b->d_items + 2 * (size_t)items;
-  a.items = items;
-  a.counter = b->d_counter;
-  a.s = make_search_args(params, out, p_stride);
-  a.ws_stride = workspace_per_cta(L.plan, b->dbytes, b->nmax, params);
-  a.s.rws_off = delta_workspace(L.plan, b->dbytes);
-  if (a.ws_stride) {
-    QAP_TRY(grow(&b->ws, &b->ws_bytes, a.ws_stride * L.grid));
-    a.ws = static_cast<unsigned char*>(b->ws);
+  const size_t total = (size_t)b->count * params->starts;
+  const bool fork = b->classes.size() > 1;
+  if (fork) QAP_CUDA(cudaEventRecord(b->fork, s));
+  for (size_t k = 0; k < b->classes.size(); ++k) {
+    const BatchClass& c = b->classes[k];
+    cudaStream_t cs = fork ? c.side : s;
+    if (fork) QAP_CUDA(cudaStreamWaitEvent(cs, b->fork, 0));
+    qapk::BatchArgs a{};
+    a.insts = b->d_insts + (size_t)nt_index(c.plan.nt) * b->count;
+    a.item_inst = b->d_class_items + c.item_off;
+    a.item_walk = b->d_class_items + total + c.item_off;
+    a.row_base = b->d_class_items + 2 * total;
+    a.items = c.items;
+    a.counter = b->d_counter + k * kCounterStride;
+    a.s = make_search_args(params, out, p_stride);
+    a.s.rws_off = delta_workspace(c.plan, b->dbytes);
+    a.ws_stride = c.ws_stride;
+    a.ws = c.ws_stride ? static_cast<unsigned char*>(b->ws) + c.ws_off : nullptr;
+    QAP_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), cs));
+    const auto fn = reinterpret_cast<qapk::BatchKernelFn>(const_cast<void*>(c.fn));
+    fn<<<c.grid, c.plan.nt, c.smem, cs>>>(a);
+    QAP_CUDA(cudaGetLastError());
+    if (fork) {
+      QAP_CUDA(cudaEventRecord(c.done, cs));
+      QAP_CUDA(cudaStreamWaitEvent(s, c.done, 0));
+    }
   }
-  QAP_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(int), s));
-  const auto fn = reinterpret_cast<qapk::BatchKernelFn>(const_cast<void*>(L.fn));
-  fn<<<L.grid, L.plan.nt, L.smem, s>>>(a);
-  QAP_CUDA(cudaGetLastError());
   return QAP_OK;
 }
 

@@ -163,3 +163,29 @@ def test_batch_with_large_instances_uses_workspace():
     for i in range(len(Fs)):
         check_instance(g, i, W, Fs[i], Ds[i], seed=4, iters=50,
                        tenure=instances.baseline_tenure(Fs[i].shape[0]))
+
+
+def test_size_classes_match_single_instance_searches():
+    """Instances of very different n take different plans (one launch per
+    size class, run on forked streams); every walk still equals the same
+    walk of a single-instance search."""
+    Fs, Ds = [], []
+    for k, n in enumerate([12, 200, 60, 13, 100, 61]):
+        F, D = instances.uniform_instance(n, 700 + k, symmetric=(k % 3 == 0))
+        Fs.append(F)
+        Ds.append(D)
+    W = 3
+    prm = q.make_params(W, seed=12, iters=120, tenure=(3, 9, 0), descend=True)
+    with q.Batch(Fs, Ds) as b:
+        pl = b.plan(prm)
+        assert pl["classes"] >= 3 and pl["pairs_per_thread"] == 40  # n = 200 leads
+        g = b.search(prm)
+        g2 = b.search(prm)  # cached classes, second launch
+    for k in FIELDS:
+        assert np.array_equal(g[k], g2[k]), k
+    for i in range(len(Fs)):
+        with q.Instance(Fs[i], Ds[i]) as inst:
+            s = inst.search(prm)
+        for k in FIELDS:
+            assert np.array_equal(g[k][i * W:(i + 1) * W], s[k]), (i, k)
+        assert np.array_equal(g["best_p"][i * W:(i + 1) * W, :Fs[i].shape[0]], s["best_p"])
