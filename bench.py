@@ -447,6 +447,8 @@ def other_workloads(args):
         iters = args.iters or w["iters"]
         b = q.Batch([i.F for i in insts], [i.D for i in insts], force_int64=True)
         prm = q.make_params(W, seed=w["seed"], iters=iters, tenure=(90, 110, 200), tenure_per_n=True)
+        # plans per size class picked by the library's autotuner (outside the timed region)
+        tune = b.autotune(prm, trial_iters=max(50, iters // 20))
         outs = b.device_outputs(W, device=dev)
         step = lambda: b.search_async(prm, outs, stream=stream)  # noqa: E731
         with torch.cuda.stream(stream):
@@ -462,11 +464,16 @@ def other_workloads(args):
                     dtype="int64", tabu_iters_per_s=float(it.sum()) / (sum(ms) / 1e3 / args.steps),
                     config={"workload": f"{len(insts)} lognormal instances, n in [20,150], "
                                         f"{W} walks x {iters} iters each",
-                            "launch": "one persistent launch, device work queue, largest n first",
-                            "threads_per_walk": plan["threads_per_walk"],
-                            "pairs_per_thread": plan["pairs_per_thread"], "grid": plan["grid"],
+                            "launch": "one persistent launch per size class, classes concurrent "
+                                      "on forked streams, device work queues, largest n first",
+                            "classes": plan["classes"],
+                            "autotuned": [{"n": [r["nmin"], r["nmax"]],
+                                           "plan": [r["threads_per_walk"], r["pairs_per_thread"]],
+                                           "workspace": bool(r["workspace"]),
+                                           "trial_ms": round(r["trial_ms"], 3),
+                                           "rule_ms": round(r["rule_ms"], 3)} for r in tune],
                             "l2": "flushed between timed steps"},
-                    gpu_launches=args.steps, clocks=clk)
+                    gpu_launches=args.steps * plan["classes"], clocks=clk)
     else:
         line.update(serve(args, q, instances))
     print(json.dumps(line))

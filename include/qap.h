@@ -292,6 +292,36 @@ qap_status qap_batch_info(const qap_batch* b, int32_t* count, int32_t* nmax,
  * of the largest n and the number of classes. */
 qap_status qap_batch_plan(qap_batch* b, const qap_search_params* params, qap_plan_info* out);
 
+/* Result of the autotuner for one size class of the rule. */
+typedef struct {
+  int32_t nmin, nmax;        /* n range of the class's instances             */
+  int32_t instances;
+  int32_t candidates;        /* plans timed                                  */
+  int32_t threads_per_walk;  /* the plan kept                                */
+  int32_t pairs_per_thread;
+  int32_t workspace;         /* 1: deltas and marks in the device workspace  */
+  float trial_ms;            /* its trial time                               */
+  float rule_ms;             /* the rule's plan's trial time                 */
+} qap_tune_result;
+
+/* Autotune the launch plans of a batch for searches like `params`.  For each
+ * size class of the rule (instances sharing the rule's plan), every compiled
+ * plan that holds the class's largest n is timed on the class's own
+ * instances: each thread count with the fewest slots that fit, and the
+ * workspace plan that keeps the deltas and tabu marks in L2/HBM instead of
+ * registers and shared memory.  The trial runs params->starts walks of
+ * `trial_iters` iterations; the fastest plan is kept for the class, and
+ * later searches with threads_per_walk = 0 use the kept plans (classes are
+ * regrouped by them).  Results are unchanged: every plan computes the same
+ * walks.  params->threads_per_walk must be 0 and launch persistent.
+ *   results   up to max_results per-class reports (may be NULL when 0)
+ *   nresults  receives the number of classes (may be NULL)
+ * Synchronous; not capturable.  Errors: QAP_EINVAL, QAP_EOVERFLOW,
+ * QAP_ENOMEM, QAP_ECUDA. */
+qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
+                              int32_t trial_iters, qap_tune_result* results,
+                              int32_t max_results, int32_t* nresults);
+
 /* Run params->starts walks of every instance.  Output row i * starts + k
  * holds walk k of instance i; best_p rows hold p_stride >= max n elements
  * (the first n[i] are the permutation).  params->launch must be

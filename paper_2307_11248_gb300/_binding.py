@@ -78,6 +78,13 @@ class PlanInfo(ctypes.Structure):
                  "sms", "classes")]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("nmin", ctypes.c_int32), ("nmax", ctypes.c_int32), ("instances", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("threads_per_walk", ctypes.c_int32),
+                ("pairs_per_thread", ctypes.c_int32), ("workspace", ctypes.c_int32),
+                ("trial_ms", ctypes.c_float), ("rule_ms", ctypes.c_float)]
+
+
 OUTPUT_FIELDS = {  # name -> (dtype, per-walk shape multiplier uses n)
     "best_p": (np.int32, True), "best_cost": (np.int64, False), "final_cost": (np.int64, False),
     "best_iter": (np.int32, False), "iters_done": (np.int32, False), "status": (np.int32, False),
@@ -128,6 +135,10 @@ def lib():
             L.qap_batch_plan.argtypes = [vp, ctypes.POINTER(SearchParams),
                                          ctypes.POINTER(PlanInfo)]
             L.qap_batch_plan.restype = st
+            L.qap_batch_autotune.argtypes = [vp, ctypes.POINTER(SearchParams), i32,
+                                             ctypes.POINTER(TuneResult), i32,
+                                             ctypes.POINTER(i32)]
+            L.qap_batch_autotune.restype = st
             L.qap_batch_search.argtypes = [vp, ctypes.POINTER(SearchParams),
                                            ctypes.POINTER(WalkOutputs), i32]
             L.qap_batch_search.restype = st
@@ -370,6 +381,16 @@ def qap_batch_plan(h, params):
     return {k: getattr(info, k) for k, _ in PlanInfo._fields_}
 
 
+def qap_batch_autotune(h, params, trial_iters=200, max_classes=64):
+    """Autotune a batch's launch plans; returns one dict per size class."""
+    res = (TuneResult * max_classes)()
+    nres = ctypes.c_int32(0)
+    _check(lib().qap_batch_autotune(h, ctypes.byref(params), int(trial_iters), res, max_classes,
+                                    ctypes.byref(nres)), "qap_batch_autotune")
+    return [{k: getattr(res[i], k) for k, _ in TuneResult._fields_}
+            for i in range(min(nres.value, max_classes))]
+
+
 def qap_batch_search(h, params, p_stride, freq=False):
     """Blocking batch search; rows i * starts + k; best_p rows of p_stride
     (with ``freq``, also W x p_stride x p_stride frequency memories)."""
@@ -430,6 +451,9 @@ class Batch:
 
     def plan(self, params):
         return qap_batch_plan(self.h, params)
+
+    def autotune(self, params, trial_iters=200):
+        return qap_batch_autotune(self.h, params, trial_iters)
 
     def search(self, params, freq=False):
         return qap_batch_search(self.h, params, self.p_stride, freq=freq)

@@ -73,6 +73,7 @@ struct qap_batch {
   int classes_threads = -1, classes_walks = 0, classes_rules = -1;
   int32_t* d_class_items = nullptr;  // per class item_inst | item_walk, then row_base
   cudaEvent_t fork = nullptr;
+  std::vector<Plan> tuned;  // per instance: the autotuner's plan (nt == 0: none)
 };
 
 namespace {
@@ -121,6 +122,40 @@ qap_status plan_batch(qap_batch* b, const qap_search_params* p, Launch* L) {
 
 int nt_index(int nt) { return nt == 128 ? 0 : nt == 256 ? 1 : nt == 512 ? 2 : 3; }
 
+// Launch shape of a class with W walks per member (smem, kernel, grid,
+// workspace) and the instance table for its thread count.
+qap_status class_shape(qap_batch* b, BatchClass& c, int W, const qap_search_params* p) {
+  std::vector<DevInstance> dm;
+  int nmax = 0;
+  for (int i : c.members) {
+    dm.push_back(b->di[i]);
+    nmax = std::max(nmax, b->di[i].n);
+  }
+  c.smem = plan_smem(c.plan, dm.data(), (int)dm.size(), b->fbytes, b->dbytes);
+  c.fn = reinterpret_cast<const void*>(pick_batch_kernel(b->dbytes, b->fbytes, c.plan));
+  if (!c.fn) return QAP_EUNSUPPORTED;
+  QAP_TRY(prepare_kernel(c.fn, c.smem));
+  int occ = 0;
+  QAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.fn, c.plan.nt, c.smem));
+  if (occ < 1) return QAP_EUNSUPPORTED;
+  c.items = (int)c.members.size() * W;
+  c.ctas_per_sm = occ;
+  c.grid = std::min(c.items, occ * b->sms);
+  c.ws_stride = workspace_per_cta(c.plan, b->dbytes, nmax, p);
+  const int t = nt_index(c.plan.nt);
+  if (!(b->insts_written & (1 << t))) {
+    std::vector<qapk::InstArgs> h(b->count);
+    char* base = static_cast<char*>(b->data);
+    for (int i = 0; i < b->count; ++i)
+      h[i] = inst_args(b->di[i], base + b->offF[i], base + b->offFt[i],
+                       reinterpret_cast<int8_t*>(base + b->offD[i]), c.plan.nt, b->fbytes);
+    QAP_CUDA(cudaMemcpy(b->d_insts + (size_t)t * b->count, h.data(),
+                        sizeof(qapk::InstArgs) * b->count, cudaMemcpyHostToDevice));
+    b->insts_written |= 1 << t;
+  }
+  return QAP_OK;
+}
+
 // Size classes of a batch search: every instance takes the plan its own n
 // would get alone, and instances with the same plan share one persistent
 // launch.  Classes run on side streams, largest n first, so the longest
@@ -136,11 +171,16 @@ qap_status plan_classes(qap_batch* b, const qap_search_params* p) {
   if ((size_t)b->count * W > (size_t)INT_MAX / 2) return QAP_EINVAL;
   b->classes_threads = -1;
   std::vector<Plan> plan_of(b->count);
-  for (int i = 0; i < b->count; ++i)
+  for (int i = 0; i < b->count; ++i) {
+    if (p->threads_per_walk == 0 && !b->tuned.empty() && b->tuned[i].nt != 0) {
+      plan_of[i] = b->tuned[i];
+      continue;
+    }
     // the batch kernel also holds one static int
     if (!choose_plan_fit(b->di[i].n, p->threads_per_walk, &b->di[i], 1, b->fbytes, b->dbytes,
                          b->smem_optin, 16, &plan_of[i]))
       return QAP_EUNSUPPORTED;
+  }
   std::vector<int> order(b->count);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
@@ -180,42 +220,14 @@ qap_status plan_classes(qap_batch* b, const qap_search_params* p) {
   int item_off = 0;
   size_t ws_off = 0;
   for (BatchClass& c : b->classes) {
-    std::vector<DevInstance> dm;
-    int nmax = 0;
-    for (int i : c.members) {
-      dm.push_back(b->di[i]);
-      nmax = std::max(nmax, b->di[i].n);
-    }
-    c.smem = plan_smem(c.plan, dm.data(), (int)dm.size(), b->fbytes, b->dbytes);
-    c.fn = reinterpret_cast<const void*>(pick_batch_kernel(b->dbytes, b->fbytes, c.plan));
-    if (!c.fn) return QAP_EUNSUPPORTED;
-    QAP_TRY(prepare_kernel(c.fn, c.smem));
-    int occ = 0;
-    QAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.fn, c.plan.nt, c.smem));
-    if (occ < 1) return QAP_EUNSUPPORTED;
-    c.items = (int)c.members.size() * W;
+    QAP_TRY(class_shape(b, c, W, p));
     c.item_off = item_off;
     item_off += c.items;
-    c.ctas_per_sm = occ;
-    c.grid = std::min(c.items, occ * b->sms);
-    c.ws_stride = workspace_per_cta(c.plan, b->dbytes, nmax, p);
     c.ws_off = ws_off;
     ws_off += (c.ws_stride * c.grid + 255) / 256 * 256;
     if (b->classes.size() > 1) {
       if (!c.side) QAP_CUDA(cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking));
       if (!c.done) QAP_CUDA(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
-    }
-    // the instance table for this thread count
-    const int t = nt_index(c.plan.nt);
-    if (!(b->insts_written & (1 << t))) {
-      std::vector<qapk::InstArgs> h(b->count);
-      char* base = static_cast<char*>(b->data);
-      for (int i = 0; i < b->count; ++i)
-        h[i] = inst_args(b->di[i], base + b->offF[i], base + b->offFt[i],
-                         reinterpret_cast<int8_t*>(base + b->offD[i]), c.plan.nt, b->fbytes);
-      QAP_CUDA(cudaMemcpy(b->d_insts + (size_t)t * b->count, h.data(),
-                          sizeof(qapk::InstArgs) * b->count, cudaMemcpyHostToDevice));
-      b->insts_written |= 1 << t;
     }
   }
   if (b->classes.size() > 1 && !b->fork)
@@ -583,6 +595,146 @@ qap_status qap_batch_plan(qap_batch* b, const qap_search_params* params, qap_pla
   out->sms = b->sms;
   out->classes = (int32_t)b->classes.size();
   return QAP_OK;
+}
+
+// The autotuner: for every size class of the rule, time each compiled plan
+// that holds the class's largest n (each thread count with its fewest slots,
+// and the workspace plan) on the class's own instances with the search's
+// walk count and `trial_iters` iterations, and keep the fastest.  Every plan
+// computes the same walks, so the choice changes only the speed.
+qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
+                              int32_t trial_iters, qap_tune_result* results,
+                              int32_t max_results, int32_t* nresults) {
+  if (!b || trial_iters < 1 || max_results < 0 || (max_results > 0 && !results))
+    return QAP_EINVAL;
+  QAP_TRY(validate_params(params));
+  if (params->launch != QAP_LAUNCH_PERSISTENT || params->threads_per_walk != 0)
+    return QAP_EINVAL;
+  qap_search_params tp = *params;
+  tp.iters = trial_iters;
+  QAP_TRY(validate_params(&tp));
+  for (const DevInstance& d : b->di) QAP_TRY(check_penalty(&tp, b->dbytes, d.bound));
+  QAP_CUDA(cudaSetDevice(b->device));
+  b->tuned.clear();
+  b->classes_threads = -1;
+  QAP_TRY(plan_classes(b, &tp));
+  struct RuleClass { Plan plan; std::vector<int> members; };
+  std::vector<RuleClass> rule;
+  for (const BatchClass& c : b->classes) rule.push_back({c.plan, c.members});
+  const int W = params->starts;
+  const size_t rows = (size_t)b->count * W;
+  QAP_TRY(grow(&b->scratch, &b->scratch_bytes, rows * 8));
+  qap_walk_outputs dout{};
+  dout.best_cost = static_cast<int64_t*>(b->scratch);
+  int32_t* d_items = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  qap_status st = QAP_OK;
+  std::vector<Plan> tuned(b->count);
+  int found = 0;
+  auto fail = [&](qap_status e) {
+    if (d_items) cudaFree(d_items);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    return e;
+  };
+  if (cudaMalloc(&d_items, (rows * 2 + b->count) * sizeof(int32_t)) != cudaSuccess)
+    return fail(QAP_ENOMEM);
+  if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
+    return fail(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
+  int* counter = b->d_counter + 63 * kCounterStride;
+  auto chk = [](cudaError_t e, const char* where) {
+    return e == cudaSuccess ? QAP_OK : cuda_fail(e, where);
+  };
+  for (const RuleClass& rc : rule) {
+    int nmin = INT_MAX, nmax = 0;
+    std::vector<DevInstance> dm;
+    for (int i : rc.members) {
+      nmin = std::min(nmin, b->di[i].n);
+      nmax = std::max(nmax, b->di[i].n);
+      dm.push_back(b->di[i]);
+    }
+    auto fits = [&](const Plan& p) {
+      return plan_smem(p, dm.data(), (int)dm.size(), b->fbytes, b->dbytes) + 16 <= b->smem_optin;
+    };
+    std::vector<Plan> cands;
+    for (int nt : {128, 256, 512, 1024}) {
+      Plan p;
+      if (nmax <= 181 && plan_for(nmax, nt, &p) && fits(p)) cands.push_back(p);
+    }
+    if (qapk::row_segments(nmax, kLargePlan.maxpt) <= kLargePlan.nt) {
+      Plan p = kLargePlan;
+      if (!fits(p)) p.store |= qapk::kGlobalFlow;
+      if (fits(p)) cands.push_back(p);
+    }
+    // items of this class, longest instances first; row bases for all
+    const size_t items = rc.members.size() * (size_t)W;
+    std::vector<int32_t> h(items * 2 + b->count);
+    size_t k = 0;
+    for (int inst : rc.members)
+      for (int w = 0; w < W; ++w, ++k) {
+        h[k] = inst;
+        h[items + k] = w;
+      }
+    for (int i = 0; i < b->count; ++i) h[2 * items + i] = i * W;
+    if ((st = chk(cudaMemcpy(d_items, h.data(), h.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice), "cudaMemcpy")) != QAP_OK)
+      return fail(st);
+    Plan best = rc.plan;
+    float best_ms = -1.f, rule_ms = -1.f;
+    for (const Plan& cand : cands) {
+      BatchClass c;
+      c.plan = cand;
+      c.members = rc.members;
+      if ((st = class_shape(b, c, W, &tp)) != QAP_OK) return fail(st);
+      if ((st = grow(&b->ws, &b->ws_bytes, c.ws_stride * c.grid)) != QAP_OK) return fail(st);
+      qapk::BatchArgs a{};
+      a.insts = b->d_insts + (size_t)nt_index(c.plan.nt) * b->count;
+      a.item_inst = d_items;
+      a.item_walk = d_items + items;
+      a.row_base = d_items + 2 * items;
+      a.items = c.items;
+      a.counter = counter;
+      a.s = make_search_args(&tp, &dout, b->nmax);
+      a.s.rws_off = delta_workspace(c.plan, b->dbytes);
+      a.ws_stride = c.ws_stride;
+      a.ws = c.ws_stride ? static_cast<unsigned char*>(b->ws) : nullptr;
+      const auto fn = reinterpret_cast<qapk::BatchKernelFn>(const_cast<void*>(c.fn));
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // a warm-up run, then the timed one
+        cudaMemsetAsync(counter, 0, sizeof(int), b->stream);
+        if (rep) cudaEventRecord(t0, b->stream);
+        fn<<<c.grid, c.plan.nt, c.smem, b->stream>>>(a);
+        if (rep) cudaEventRecord(t1, b->stream);
+      }
+      if ((st = chk(cudaEventSynchronize(t1), "autotune trial")) != QAP_OK) return fail(st);
+      cudaEventElapsedTime(&ms, t0, t1);
+      const bool is_rule = cand.nt == rc.plan.nt && cand.maxpt == rc.plan.maxpt &&
+                           cand.store == rc.plan.store;
+      if (is_rule) rule_ms = ms;
+      if (best_ms < 0.f || ms < best_ms) {
+        best_ms = ms;
+        best = cand;
+      }
+    }
+    for (int i : rc.members) tuned[i] = best;
+    if (found < max_results) {
+      qap_tune_result& r = results[found];
+      r.nmin = nmin;
+      r.nmax = nmax;
+      r.instances = (int32_t)rc.members.size();
+      r.candidates = (int32_t)cands.size();
+      r.threads_per_walk = best.nt;
+      r.pairs_per_thread = best.maxpt;
+      r.workspace = best.store != 0;
+      r.trial_ms = best_ms;
+      r.rule_ms = rule_ms;
+    }
+    ++found;
+  }
+  if (nresults) *nresults = found;
+  b->tuned = tuned;
+  b->classes_threads = -1;  // the next search regroups by the tuned plans
+  return fail(QAP_OK);
 }
 
 qap_status qap_batch_search_async(qap_batch* b, const qap_search_params* params,

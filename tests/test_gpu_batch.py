@@ -189,3 +189,40 @@ def test_size_classes_match_single_instance_searches():
         for k in FIELDS:
             assert np.array_equal(g[k][i * W:(i + 1) * W], s[k]), (i, k)
         assert np.array_equal(g["best_p"][i * W:(i + 1) * W, :Fs[i].shape[0]], s["best_p"])
+
+
+def test_autotune_keeps_results_and_reports_classes():
+    """The autotuner times every plan that holds each size class and keeps
+    the fastest; the walks it then runs are the same walks."""
+    Fs, Ds = [], []
+    for k, n in enumerate([20, 95, 100, 45, 190]):
+        F, D = instances.uniform_instance(n, 40 + k, symmetric=(k % 2 == 1))
+        Fs.append(F)
+        Ds.append(D)
+    W = 8
+    prm = q.make_params(W, seed=21, iters=150, tenure=(5, 15, 0))
+    with q.Batch(Fs, Ds) as b:
+        before = b.search(prm)
+        report = b.autotune(prm, trial_iters=60)
+        after = b.search(prm)
+        pl = b.plan(prm)
+    assert len(report) >= 3
+    assert sum(r["instances"] for r in report) == len(Fs)
+    for r in report:
+        assert r["candidates"] >= 1 and r["trial_ms"] > 0
+        assert r["trial_ms"] <= r["rule_ms"] or r["rule_ms"] < 0
+    assert any(r["candidates"] >= 2 for r in report)
+    assert pl["classes"] >= 1
+    for k in FIELDS:
+        assert np.array_equal(before[k], after[k]), k
+    for i, F in enumerate(Fs):  # best_p rows beyond n are padding
+        rows = slice(i * W, (i + 1) * W)
+        assert np.array_equal(before["best_p"][rows, :F.shape[0]], after["best_p"][rows, :F.shape[0]])
+
+
+def test_autotune_rejects_fixed_thread_counts():
+    F, D = instances.uniform_instance(30, 1, symmetric=False)
+    with q.Batch([F], [D]) as b:
+        with pytest.raises(q.QapError) as e:
+            b.autotune(q.make_params(2, seed=1, iters=10, tenure=(1, 2, 0), threads_per_walk=256))
+        assert e.value.status == q.EINVAL
