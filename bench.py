@@ -167,6 +167,24 @@ def dist_setup():
     return world, rank, local
 
 
+def replica_walk_base(rank, walks_per_rank):
+    """Walk ids of rank r are r*W .. r*W + W - 1: replicas search disjoint
+    walks whose union is the one-process search of N*W walks."""
+    return rank * walks_per_rank
+
+
+def combine_ranks(total_ms, evals_rank, device):
+    """Whole-job figures: the slowest rank's time and the sum of all ranks'
+    evaluations (torch.distributed when it is initialised, else this rank's)."""
+    import torch
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    evals = torch.tensor([evals_rank], dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(evals, op=torch.distributed.ReduceOp.SUM)
+    return tmax.item(), evals.item()
+
+
 def run_reference(args, world, rank):
     """The oracle (CPU), timed on the host cores: each step is a bounded
     sample of the workload (the first `ref_walks` walks, full iterations)."""
@@ -215,7 +233,8 @@ def main():
     ap.add_argument("--iters", type=int, default=0,
                     help="override the iteration count (smaller cases for profiling)")
     ap.add_argument("--walks", type=int, default=0, help="override the walk count")
-    ap.add_argument("--workload", choices=["asym50", "grid100", "batch512", "serve"],
+    ap.add_argument("--workload", choices=["asym50", "sym12", "grid100", "batch512", "serve",
+                                           "sweep"],
                     default="asym50",
                     help="asym50 is the benchmark line; the others measure the remaining "
                          "workloads (one JSON line each)")
@@ -245,7 +264,8 @@ def main():
 
     inst = q.Instance(w["F"], w["D"])
     prm = q.make_params(W, seed=w["seed"], iters=iters, tenure=w["tenure"], aspiration=True,
-                        walk_base=rank * W, threads_per_walk=args.threads_per_walk)
+                        walk_base=replica_walk_base(rank, W),
+                        threads_per_walk=args.threads_per_walk)
     plan = inst.plan(prm)
     outs = inst.device_outputs(W, device=dev)
 
@@ -279,20 +299,17 @@ def main():
     total_ms = sum(step_ms)
     iters_done = outs["iters_done"].sum().item()
     evals_rank = float(iters_done) * T * args.steps
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    evals_all = torch.tensor([evals_rank], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(evals_all, op=torch.distributed.ReduceOp.SUM)
-    total_s = tmax.item() / 1e3
-    value = evals_all.item() / total_s
+    max_ms, evals_all = combine_ranks(total_ms, evals_rank, dev)
+    total_s = max_ms / 1e3
+    value = evals_all / total_s
     clk = clocks.summary()
 
     # ---- plain form: one launch per walk (same kernel body), one step
     plain = None
     if not args.no_plain and rank == 0:
         pprm = q.make_params(W, seed=w["seed"], iters=iters, tenure=w["tenure"],
-                             aspiration=True, walk_base=rank * W, launch=q.LAUNCH_PLAIN,
+                             aspiration=True, walk_base=replica_walk_base(rank, W),
+                             launch=q.LAUNCH_PLAIN,
                              threads_per_walk=args.threads_per_walk)
         pouts = inst.device_outputs(W, device=dev)
         with torch.cuda.stream(stream):
@@ -474,9 +491,127 @@ def other_workloads(args):
                                            "rule_ms": round(r["rule_ms"], 3)} for r in tune],
                             "l2": "flushed between timed steps"},
                     gpu_launches=args.steps * plan["classes"], clocks=clk)
+    elif args.workload == "sym12":
+        line.update(sym12(args, q, instances, stream, flush, dev))
+    elif args.workload == "sweep":
+        line.update(sweep(args, q, instances, stream, dev))
     else:
         line.update(serve(args, q, instances))
     print(json.dumps(line))
+
+
+def sym12(args, q, instances, stream, flush, dev):
+    """n = 12 symmetric, 2opt to local minima from 32 starts: the latency
+    case.  One persistent launch (batched) against one launch per walk
+    (plain), and the oracle on the host cores."""
+    import torch
+    import oracle
+    w = instances.workload_sym12()
+    n, W = w["F"].shape[0], w["walks"]
+    T = n * (n - 1) // 2
+    inst = q.Instance(w["F"], w["D"])
+    res = {}
+    for form, launch in (("batched", q.LAUNCH_PERSISTENT), ("plain", q.LAUNCH_PLAIN)):
+        prm = q.make_params(W, seed=w["seed"], descend=True, launch=launch)
+        outs = inst.device_outputs(W, device=dev)
+        step = lambda: inst.search_async(prm, outs, stream=stream)  # noqa: E731
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+        ms, clk = timed_steps(step, args.steps, stream, flush, dev)
+        moves = float(outs["descent_moves"].sum().item())
+        res[form] = dict(ms=sum(ms) / args.steps, moves=moves, clk=clk)
+    oracle.build()
+    t0 = time.perf_counter()
+    o = oracle.run_walks(w["F"], w["D"], W, seed=w["seed"], descend=True)
+    cpu_s = time.perf_counter() - t0
+    b = res["batched"]
+    return dict(metric="2opt to local minima, 32 starts: latency and swap-delta evals/s",
+                value=b["moves"] * T / (b["ms"] / 1e3), ms_per_step=b["ms"], steps=args.steps,
+                warmup=args.warmup, dtype="int32",
+                plain={"ms_per_step": res["plain"]["ms"], "launches_per_step": W},
+                batched_over_plain=res["plain"]["ms"] / b["ms"],
+                cpu_baseline={"kind": "oracle", "ms": cpu_s * 1e3, "cores": oracle.num_threads(),
+                              "identical_moves": int(o["descent_moves"].sum()) == int(b["moves"])},
+                config={"workload": "sym12: n=12 symmetric uniform[0,99], 2opt from 32 starts",
+                        "launch": "persistent, one launch per step", "l2": "flushed between steps"},
+                gpu_launches=args.steps, clocks=b["clk"])
+
+
+def sweep(args, q, instances, stream, dev):
+    """Tabu sensitivity to the iteration budget, the walk count and the seed
+    (the paper's Section 6.6, Figs. 7-9), on the asym50 stand-in and on one
+    int64 lognormal instance of the batch family, plus 2opt on the GPU
+    against the oracle on the host cores (Fig. 4).  Gap = (best of the walks
+    - best known) / best known, the best known being the lowest cost any run
+    here found (including a 1024 x 20000 reference run)."""
+    import torch
+    import oracle
+
+    def run(inst, W, iters, seed, tn, descend=False):
+        prm = q.make_params(W, seed=seed, iters=iters, tenure=tn, descend=descend)
+        outs = inst.device_outputs(W, device=dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            inst.search_async(prm, outs, stream=stream)
+            b.record(stream)
+        stream.synchronize()
+        return int(outs["best_cost"].min().item()), a.elapsed_time(b)
+
+    out = {}
+    lognormal = instances.lognormal_instance(100, 77, symmetric=False)
+    for name, (F, D), f64 in (("asym50", (instances.workload_asym50()["F"],
+                                          instances.workload_asym50()["D"]), False),
+                              ("lognormal100", lognormal, True)):
+        n = F.shape[0]
+        tn = instances.baseline_tenure(n)
+        inst = q.Instance(F, D, force_int64=f64)
+        run(inst, 64, 100, 1, tn)  # warm-up
+        rows = []
+        ref, _ = run(inst, 1024, 20000, 999, tn)
+        for iters in (500, 1000, 2000, 5000, 10000, 20000):
+            for seed in (1, 2, 3):
+                c, ms = run(inst, 256, iters, seed, tn)
+                rows.append(("iters", iters, 256, seed, c, ms))
+        for W in (32, 64, 128, 256, 512, 1024):
+            for seed in (1, 2, 3):
+                c, ms = run(inst, W, 5000, seed, tn)
+                rows.append(("walks", 5000, W, seed, c, ms))
+        for seed in range(10, 18):
+            c, ms = run(inst, 256, 5000, seed, tn)
+            rows.append(("seeds", 5000, 256, seed, c, ms))
+        best = min([ref] + [r[4] for r in rows])
+        table = {}
+        for kind, iters, W, seed, c, ms in rows:
+            key = f"{kind}:{iters}x{W}"
+            t = table.setdefault(key, {"iters": iters, "walks": W, "gaps_pct": [], "ms": []})
+            t["gaps_pct"].append(round(100.0 * (c - best) / best, 4))
+            t["ms"].append(round(ms, 2))
+        out[name] = {"n": n, "best_known": best, "reference_run": "1024 walks x 20000 iters",
+                     "tenure": list(tn), "rows": table}
+        inst.close()
+    # 2opt: GPU (32 starts, one launch) against the oracle on all host cores
+    fig4 = []
+    oracle.build()
+    for n in (30, 50, 80, 100):
+        F, D = instances.uniform_instance(n, 300 + n, symmetric=False)
+        inst = q.Instance(F, D)
+        run(inst, 32, 0, 5, (1, 1, 0), descend=True)
+        _, ms = run(inst, 32, 0, 5, (1, 1, 0), descend=True)
+        inst.close()
+        t0 = time.perf_counter()
+        oracle.run_walks(F, D, 32, seed=5, descend=True)
+        cpu_ms = (time.perf_counter() - t0) * 1e3
+        fig4.append({"n": n, "gpu_ms": round(ms, 3), "cpu_oracle_ms": round(cpu_ms, 2),
+                     "cpu_threads": oracle.num_threads()})
+    return dict(metric="tabu solution-quality gap vs iterations, walks and seeds; 2opt GPU vs CPU",
+                value=None, unit="gap %", higher_is_better=False, dtype="int32/int64",
+                sweeps=out, two_opt_vs_cpu=fig4,
+                config={"workload": "asym50 and a lognormal n=100 instance (int64); "
+                                    "2opt on uniform n in {30,50,80,100}"},
+                gpu_launches=None)
 
 
 def serve(args, q, instances):
