@@ -110,8 +110,10 @@ class ClockSampler:
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
-# the sources that make the int8-flow walk kernel (the profiled one)
-KERNEL_SOURCES = ("qap_kernels.cuh", "qap_philox.cuh", "qap_walk_i32_f8.cu")
+# the sources that make the int8-flow walk kernels (the profiled one is the
+# products form, qap_walk_i32_f8m.cu)
+KERNEL_SOURCES = ("qap_kernels.cuh", "qap_philox.cuh", "qap_walk_i32_f8.cu",
+                  "qap_walk_i32_f8m.cu")
 
 
 def kernel_source_hash():
@@ -487,6 +489,7 @@ def other_workloads(args):
                             "autotuned": [{"n": [r["nmin"], r["nmax"]],
                                            "plan": [r["threads_per_walk"], r["pairs_per_thread"]],
                                            "workspace": bool(r["workspace"]),
+                                           "products": bool(r["products"]),
                                            "trial_ms": round(r["trial_ms"], 3),
                                            "rule_ms": round(r["rule_ms"], 3)} for r in tune],
                             "l2": "flushed between timed steps"},

@@ -243,6 +243,9 @@ typedef struct {
   int32_t sms;
   int32_t classes;           /* launches of a batch search (size classes);
                                 1 for one instance                          */
+  int32_t products;          /* 1: phase X from products kept in shared
+                                memory (int8 flows, when they fit)          */
+  int32_t workspace;         /* 1: deltas and marks in the device workspace */
 } qap_plan_info;
 qap_status qap_plan(qap_ctx* ctx, const qap_search_params* params, qap_plan_info* out);
 
@@ -300,6 +303,7 @@ typedef struct {
   int32_t threads_per_walk;  /* the plan kept                                */
   int32_t pairs_per_thread;
   int32_t workspace;         /* 1: deltas and marks in the device workspace  */
+  int32_t products;          /* 1: phase X from maintained products          */
   float trial_ms;            /* its trial time                               */
   float rule_ms;             /* the rule's plan's trial time                 */
 } qap_tune_result;
@@ -307,9 +311,11 @@ typedef struct {
 /* Autotune the launch plans of a batch for searches like `params`.  For each
  * size class of the rule (instances sharing the rule's plan), every compiled
  * plan that holds the class's largest n is timed on the class's own
- * instances: each thread count with the fewest slots that fit, and the
- * workspace plan that keeps the deltas and tabu marks in L2/HBM instead of
- * registers and shared memory.  The trial runs params->starts walks of
+ * instances: each thread count with the fewest slots that fit (with int8
+ * flows also in its products form, which keeps the n x n dot products of
+ * phase X in shared memory and updates them per move), and the workspace
+ * plan that keeps the deltas and tabu marks in L2/HBM instead of registers
+ * and shared memory.  The trial runs params->starts walks of
  * `trial_iters` iterations; the fastest plan is kept for the class, and
  * later searches with threads_per_walk = 0 use the kept plans (classes are
  * regrouped by them).  Results are unchanged: every plan computes the same

@@ -75,14 +75,15 @@ class ServerStats(ctypes.Structure):
 class PlanInfo(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in
                 ("threads_per_walk", "pairs_per_thread", "smem_bytes", "grid", "ctas_per_sm",
-                 "sms", "classes")]
+                 "sms", "classes", "products", "workspace")]
 
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("nmin", ctypes.c_int32), ("nmax", ctypes.c_int32), ("instances", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("threads_per_walk", ctypes.c_int32),
                 ("pairs_per_thread", ctypes.c_int32), ("workspace", ctypes.c_int32),
-                ("trial_ms", ctypes.c_float), ("rule_ms", ctypes.c_float)]
+                ("products", ctypes.c_int32), ("trial_ms", ctypes.c_float),
+                ("rule_ms", ctypes.c_float)]
 
 
 OUTPUT_FIELDS = {  # name -> (dtype, per-walk shape multiplier uses n)

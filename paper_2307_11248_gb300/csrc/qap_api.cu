@@ -351,6 +351,8 @@ qap_status qap_plan(qap_ctx* ctx, const qap_search_params* params, qap_plan_info
   out->ctas_per_sm = L.ctas_per_sm;
   out->sms = ctx->sms;
   out->classes = 1;
+  out->products = (L.plan.store & qapk::kProductM) != 0;
+  out->workspace = (L.plan.store & qapk::kGlobalDelta) != 0;
   return QAP_OK;
 }
 
@@ -594,6 +596,8 @@ qap_status qap_batch_plan(qap_batch* b, const qap_search_params* params, qap_pla
   out->ctas_per_sm = c.ctas_per_sm;
   out->sms = b->sms;
   out->classes = (int32_t)b->classes.size();
+  out->products = (c.plan.store & qapk::kProductM) != 0;
+  out->workspace = (c.plan.store & qapk::kGlobalDelta) != 0;
   return QAP_OK;
 }
 
@@ -659,7 +663,13 @@ qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
     std::vector<Plan> cands;
     for (int nt : {128, 256, 512, 1024}) {
       Plan p;
-      if (nmax <= 181 && plan_for(nmax, nt, &p) && fits(p)) cands.push_back(p);
+      if (nmax <= 181 && plan_for(nmax, nt, &p) && fits(p)) {
+        cands.push_back(p);
+        Plan m = p;
+        m.store |= qapk::kProductM;
+        if (b->fbytes == 1 && b->dbytes == 4 && has_product_form(p) && fits(m))
+          cands.push_back(m);
+      }
     }
     if (qapk::row_segments(nmax, kLargePlan.maxpt) <= kLargePlan.nt) {
       Plan p = kLargePlan;
@@ -725,7 +735,8 @@ qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
       r.candidates = (int32_t)cands.size();
       r.threads_per_walk = best.nt;
       r.pairs_per_thread = best.maxpt;
-      r.workspace = best.store != 0;
+      r.workspace = (best.store & qapk::kGlobalDelta) != 0;
+      r.products = (best.store & qapk::kProductM) != 0;
       r.trial_ms = best_ms;
       r.rule_ms = rule_ms;
     }
@@ -872,7 +883,7 @@ extern "C" qap_status qap_batch_search_noalloc(qap_batch* b, const qap_search_pa
   QAP_TRY(noalloc_scratch(b->device, &base));
   Launch L;
   QAP_TRY(plan_batch(b, params, &L));
-  if (L.plan.store != 0) {
+  if (L.plan.store & (qapk::kGlobalDelta | qapk::kGlobalFlow)) {
     snprintf(g_last_error, sizeof(g_last_error),
              "qap_batch_search_noalloc: n = %d needs the large-n plan, whose workspace is "
              "allocated; the no-allocation form holds n <= 181", b->nmax);

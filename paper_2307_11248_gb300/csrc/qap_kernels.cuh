@@ -116,13 +116,22 @@ struct BatchArgs {
 // F^T from global memory (L1-cached), leaving shared memory to P and P^T.
 constexpr int kGlobalDelta = 1;
 constexpr int kGlobalFlow = 2;
+// Plans with bit kProductM (int8 flows) keep the n x n products
+//   M[x][k] = sum_j F[x][j] P[k][j] + F[j][x] P[j][k]
+// in shared memory and update them after each move (see phase_m_update),
+// so that phase X reads the dot products it needs instead of computing them.
+constexpr int kProductM = 4;
+
+// row stride of M in int32 words: whole 16-byte groups, an odd number of
+// them (rows read side by side by consecutive threads spread over banks)
+__host__ __device__ inline int ld_m(int n) { return 4 * (((n + 3) / 4) | 1); }
 
 // ---------------------------------------------------------------------------
 // shared-memory layout (host and device agree through this function)
 // ---------------------------------------------------------------------------
 struct SmemLayout {
   int offF, offFt, offP, offPt, offTabu, offVec, offR, offG0, offG1, offPerm, offBest, offRedD,
-      offRedK, offSum;
+      offRedK, offSum, offM;
   int bytes;
 };
 
@@ -149,6 +158,8 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int ldF, int fbytes, in
   L.offRedD = o; o = align16(o + 32 * 8);
   L.offRedK = o; o = align16(o + 32 * 4);
   L.offSum = o;  o = align16(o + 32 * 8);
+  // M twice (current and next) and the update words of the indices
+  L.offM = o;    o = (store & kProductM) ? align16(o + 2 * n * ld_m(n) * 4 + ld_m(n) * 4) : o;
   L.bytes = o;
   return L;
 }
@@ -308,6 +319,7 @@ struct WalkSmem {
   DT* redD;
   uint32_t* redK;
   int64_t* sum;
+  int32_t* M;  // kProductM plans: two n x ld_m(n) buffers, then ld_m(n) words
 };
 
 // Eq. 2 (with the diagonal term) for the pair {x, k}, by one thread, from the
@@ -512,6 +524,130 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Phase X from maintained products (plans with kProductM, int8 flows)
+// ---------------------------------------------------------------------------
+// M from the current P into buffer Mc, at the start of a walk: one dot
+// product per entry (two when F or D is asymmetric).  M[k][k] is g[k].
+template <int NT>
+__device__ __forceinline__ void compute_m(const WalkSmem<int32_t, int8_t>& S, int32_t* Mc, int n,
+                                          int ldF, int ldP, bool sym) {
+  using C = Chunk<int8_t>;
+  const int nc = (n + C::W - 1) / C::W, ldm = ld_m(n);
+  for (int e = threadIdx.x; e < n * n; e += NT) {
+    const int x = e / n, k = e - (e / n) * n;
+    const auto* Fx = reinterpret_cast<const C::FV*>(S.F + x * ldF);
+    const auto* Pk = reinterpret_cast<const C::QV*>(S.P + k * ldP);
+    const auto* Ftx = reinterpret_cast<const C::FV*>(S.Ft + x * ldF);
+    const auto* Ptk = reinterpret_cast<const C::QV*>(S.Pt + k * ldP);
+    int acc = 0;
+    for (int c = 0; c < nc; ++c) {
+      acc = C::dot(Fx[c], Pk[c], acc);
+      if (!sym) acc = C::dot(Ftx[c], Ptk[c], acc);
+    }
+    Mc[x * ldm + k] = sym ? 2 * acc : acc;
+  }
+}
+
+// Phase X of move (r, s) from M (pre-move, buffer Mc): one thread per index
+// k writes the update vector of k (also as one word in vw, for
+// phase_m_update) and, for k outside {r, s}, the recomputed deltas of the
+// pairs {r, k} and {s, k}, whose dot products are the entries
+//   F[r].Q[k] + F^T[r].Q^T[k] = M[r][k],  F[k].Q[s] + F^T[k].Q^T[s] = M[k][s]
+// (and the same with r, s exchanged); the threads of k = r and k = s write
+// g'[r] = M'[r][r] and g'[s] = M'[s][s] (see phase_m_update).  The finish
+// is the one of phase_x.
+template <typename DT, int NT>
+__device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, int8_t>& S, const int32_t* M,
+                                             int32_t* vw, DT* gn, int n, int ldF, int ldP, int r,
+                                             int s) {
+  using VO = VecOps<int8_t>;
+  const int8_t* F = S.F;
+  const int8_t* Ft = S.Ft;
+  const int8_t* Q = S.P;
+  const int8_t* Qt = S.Pt;
+  const int ldm = ld_m(n);
+  for (int k = threadIdx.x; k < n; k += NT) {
+    const int Frk = F[r * ldF + k], Fsk = F[s * ldF + k];
+    const int Fkr = Ft[r * ldF + k], Fks = Ft[s * ldF + k];
+    const int Qrk = Q[r * ldP + k], Qsk = Q[s * ldP + k];
+    const int Qkr = Qt[r * ldP + k], Qks = Qt[s * ldP + k];
+    const int a = Frk - Fsk, b = Qrk - Qsk, c = Fkr - Fks, e = Qkr - Qks;
+    const typename VO::V v = VO::pack(a, b, c, e);
+    reinterpret_cast<typename VO::V*>(S.vec)[k] = v;
+    vw[k] = v.x;
+    if (k == r || k == s) {
+      // g'[x] = M[x][xb] - c_x e_xb - a_x b_xb, xb the other of r, s
+      const int xb = k == s ? r : s;
+      const int exb = Qt[r * ldP + xb] - Qt[s * ldP + xb];
+      const int bxb = Q[r * ldP + xb] - Q[s * ldP + xb];
+      gn[k] = (DT)M[k * ldm + xb] - (DT)(c * exb) - (DT)(a * bxb);
+      continue;
+    }
+    const int fRR = F[r * ldF + r], fRS = F[r * ldF + s];
+    const int fSR = F[s * ldF + r], fSS = F[s * ldF + s];
+    const int qRR = Q[r * ldP + r], qRS = Q[r * ldP + s];
+    const int qSR = Q[s * ldP + r], qSS = Q[s * ldP + s];
+    const int Fkk = F[k * ldF + k], Qkk = Q[k * ldP + k];
+    const DT gk = (DT)M[k * ldm + k] - (DT)(a * b) - (DT)(c * e);
+#pragma unroll
+    for (int xi = 0; xi < 2; ++xi) {
+      const bool xs = xi != 0;
+      const int fxx = xs ? fSS : fRR;   // F[x][x]
+      const int pxx = xs ? qRR : qSS;   // P'[x][x] = Q[xb][xb]
+      const int fxk = xs ? Fsk : Frk;   // F[x][k]
+      const int fkx = xs ? Fks : Fkr;   // F[k][x]
+      const int pxk = xs ? Qrk : Qsk;   // P'[x][k] = Q[xb][k]
+      const int pkx = xs ? Qkr : Qks;   // P'[k][x] = Q[k][xb]
+      const int fx_rs = xs ? fSR - fSS : fRR - fRS;
+      const int frs_x = xs ? fRS - fSS : fRR - fSR;
+      const int qxb_sr = xs ? qRS - qRR : qSS - qSR;
+      const int qsr_xb = xs ? qSR - qRR : qSS - qRS;
+      const int corr = (fxx - fxk - fkx + Fkk) * (pxx - pxk - pkx + Qkk);
+      const int sig = -fx_rs * e - frs_x * b + qxb_sr * c + qsr_xb * a;
+      const int Ax = M[(xs ? s : r) * ldm + k];
+      const int Bx = M[k * ldm + (xs ? r : s)];
+      S.R[xi * n + k] = (DT)Ax + (DT)Bx + (DT)sig - gk + (DT)corr;
+    }
+  }
+}
+
+// M after move (r, s), from Mc into Mn, with the update words vw of
+// phase_m_prep:
+//   M'[x][k] = M[x][t(k)] - a_x b_t(k) - c_x e_t(k),  t the transposition
+// (r s): with P'[i][j] = P[t(i)][t(j)], the row-x terms change only at
+// j in {r, s}.  A thread takes 4 consecutive entries of a row (16-byte
+// loads and stores); columns r and s take the other column's entry and
+// word.  Runs beside the owner pass, which does not read M; the next
+// iteration reads Mn after its arg-min barrier.  Columns past n are padding.
+template <int NT>
+__device__ __forceinline__ void phase_m_update(const int32_t* Mc, int32_t* Mn, const int32_t* vw,
+                                               int n, int r, int s) {
+  const int ldm = ld_m(n), gpr = ldm / 4;
+  const int4* vw4 = reinterpret_cast<const int4*>(vw);
+  for (int item = threadIdx.x; item < n * gpr; item += NT) {
+    const int x = item / gpr, g = item - (item / gpr) * gpr;
+    const int k0 = 4 * g;
+    // bytes (a_x, c_x, 0, 0) against (b, e, a, c) of each column
+    const int ux = (int)__byte_perm((uint32_t)vw[x], 0u, 0x4432u);
+    int4 m = reinterpret_cast<const int4*>(Mc + x * ldm)[g];
+    int4 w = vw4[g];
+    if ((unsigned)(r - k0) < 4u || (unsigned)(s - k0) < 4u) {
+      const int msr = Mc[x * ldm + s], mrs = Mc[x * ldm + r];
+      const int wsr = vw[s], wrs = vw[r];
+      if (k0 + 0 == r) { m.x = msr; w.x = wsr; } else if (k0 + 0 == s) { m.x = mrs; w.x = wrs; }
+      if (k0 + 1 == r) { m.y = msr; w.y = wsr; } else if (k0 + 1 == s) { m.y = mrs; w.y = wrs; }
+      if (k0 + 2 == r) { m.z = msr; w.z = wsr; } else if (k0 + 2 == s) { m.z = mrs; w.z = wrs; }
+      if (k0 + 3 == r) { m.w = msr; w.w = wsr; } else if (k0 + 3 == s) { m.w = mrs; w.w = wrs; }
+    }
+    m.x -= __dp4a(ux, w.x, 0);
+    m.y -= __dp4a(ux, w.y, 0);
+    m.z -= __dp4a(ux, w.z, 0);
+    m.w -= __dp4a(ux, w.w, 0);
+    reinterpret_cast<int4*>(Mn + x * ldm)[g] = m;
+  }
+}
+
 // Exchange rows and columns r, s of P (and P^T) and p[r], p[s], so that
 // P'[i][j] = P[s(i)][s(j)] with s the transposition (r s).  Column entries of
 // the other rows: one thread per (matrix, row); rows r and s: 4-byte words by
@@ -626,6 +762,7 @@ __device__ __forceinline__ WalkSmem<DT, FE> smem_views(unsigned char* smem, cons
   S.redD = reinterpret_cast<DT*>(smem + L.offRedD);
   S.redK = reinterpret_cast<uint32_t*>(smem + L.offRedK);
   S.sum = reinterpret_cast<int64_t*>(smem + L.offSum);
+  S.M = (STORE & kProductM) ? reinterpret_cast<int32_t*>(smem + L.offM) : nullptr;
   return S;
 }
 
@@ -725,7 +862,14 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     c0 += (int64_t)S.F[i * ldF + j] * (int64_t)S.P[i * ldP + j];
   }
   c0 = block_sum<NT>(c0, S.sum);
-  compute_g<DT, FE, NT>(S, S.g0, n, ldF, ldP, sym, G);
+  // maintained products: current and next buffers, and the update words
+  int32_t* Mc = S.M;
+  int32_t* Mn = S.M ? S.M + n * ld_m(n) : nullptr;
+  int32_t* const vw = S.M ? S.M + 2 * n * ld_m(n) : nullptr;
+  if constexpr ((STORE & kProductM) != 0)
+    compute_m<NT>(S, Mc, n, ldF, ldP, sym);
+  else
+    compute_g<DT, FE, NT>(S, S.g0, n, ldF, ldP, sym, G);
   DeltaSlots<DT, NT, MAXPT, (STORE & kGlobalDelta) != 0> dl(ws);
   // owner pass form: the O(1) update everywhere, then the rows r and s
   // apart (register slots), or one pass choosing per slot (workspace slots,
@@ -865,6 +1009,15 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     if (tabu && su == r && s >= sv && s < sv + slen) S.tabu[(s - sv) * NT + tid] = stamp;
   };
 
+  // Phase X of move (r, s): from the maintained products (kProductM), or
+  // by dot products over the rows of F and P.
+  auto phase_x_any = [&](int r, int s) {
+    if constexpr ((STORE & kProductM) != 0)
+      phase_m_prep<DT, NT>(S, Mc, vw, gn, n, ldF, ldP, r, s);
+    else
+      phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
+  };
+
   // ---- 2opt descent (Section 4.1): best move while it improves.
   if (a.descend) {
     // A descent strictly lowers the cost at every move, so it ends; the
@@ -886,8 +1039,14 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       cur += bd;
       ++dmoves;
       if (warp0) dh = fnv_step(dh, r, s);
-      phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
+      phase_x_any(r, s);
       __syncthreads();
+      if constexpr ((STORE & kProductM) != 0) {
+        phase_m_update<NT>(Mc, Mn, vw, n, r, s);
+        int32_t* t = Mc;
+        Mc = Mn;
+        Mn = t;
+      }
       update_and_scan(std::false_type{}, r, s, false, 0, 0, cur, cur, bd, bk);
       swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
       DT* t = gc; gc = gn; gn = t;
@@ -975,8 +1134,14 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         tenure = tmin + (int)below(x, (uint32_t)(tmax - tmin + 1));
         tleft = period;
       }
-      phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
+      phase_x_any(r, s);
       __syncthreads();
+      if constexpr ((STORE & kProductM) != 0) {
+        phase_m_update<NT>(Mc, Mn, vw, n, r, s);
+        int32_t* t = Mc;
+        Mc = Mn;
+        Mn = t;
+      }
       int stamp = it + tenure;
       const bool owner = su == r && s >= sv && s < sv + slen;
       if (period == 0 && (owner || (EXT && a.crit != 0))) {

@@ -5,6 +5,8 @@
 
 namespace qapk {
 
+WalkKernelFn walk_kernel_i32_f8m(int nt, int maxpt, int store);  // qap_walk_i32_f8m.cu
+
 #define QAP_PLANS(K)                                             \
   switch (nt * 1000 + maxpt * 10 + store) {                      \
     case 128040: return K<DT, FE, 128, 4, 0>;                    \
@@ -26,6 +28,7 @@ namespace qapk {
 WalkKernelFn walk_kernel_i32_f8(int nt, int maxpt, int store) {
   using DT = int32_t;
   using FE = int8_t;
+  if (store & kProductM) return walk_kernel_i32_f8m(nt, maxpt, store);
   QAP_PLANS(walk_kernel)
 }
 

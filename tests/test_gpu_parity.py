@@ -316,3 +316,19 @@ def test_async_search_in_cuda_graph(gpu):
     o = oracle.run_walks(w["F"], w["D"], 16, seed=w["seed"], iters=300, tenure=w["tenure"])
     assert np.array_equal(first["best_cost"].cpu().numpy(), o["best_cost"])
     assert np.array_equal(first["hash"].cpu().numpy().view(np.uint64), o["hash"])
+
+
+@pytest.mark.parametrize("n,sym,products", [(50, False, 1), (100, False, 1), (50, True, 0),
+                                            (170, False, 0)])
+def test_phase_x_forms_bit_exact(n, sym, products):
+    """Phase X from maintained products (int8 flows, asymmetric, when M fits
+    shared memory) and by dot products (the rest): both equal the oracle."""
+    F, D = instances.uniform_instance(n, 420 + n, symmetric=sym)
+    prm = q.make_params(4, seed=13, iters=200, tenure=(3, 9, 0), descend=True)
+    with q.Instance(F, D) as inst:
+        assert inst.plan(prm)["products"] == products
+        g = inst.search(prm)
+    o = oracle.run_walks(F, D, 4, seed=13, iters=200, tenure=(3, 9, 0), descend=True)
+    for k in ["best_p", "best_cost", "final_cost", "best_iter", "iters_done", "hash",
+              "descent_hash", "descent_moves"]:
+        assert np.array_equal(g[k].astype(np.int64), o[k].astype(np.int64)), k
