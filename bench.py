@@ -649,6 +649,7 @@ def serve(args, q, instances):
         for r in warm:
             sv.wait(sv.submit(r.inst.F, r.inst.D, q.make_params(
                 32, seed=r.rid, iters=200, tenure=instances.baseline_tenure(r.inst.n))))
+        run(0, sv)                        # grows every slot's pinned buffers and the arena
         saturated = run(0, sv)            # all at once: capacity
         offered = run(2000.0, sv)         # the offered Poisson rate
         rate80 = 0.8 * saturated["solves_per_s"]
@@ -665,7 +666,7 @@ def serve(args, q, instances):
             "config": {"workload": f"{count} Poisson requests (2000/s offered), n in [12,256], "
                                    "generators sym uniform / asym uniform / grid",
                        "server": "64 slots, 2 GiB arena, FIFO admission by slot and memory"},
-            "gpu_launches": 3 * count}
+            "gpu_launches": 4 * count}
 
 
 if __name__ == "__main__":
