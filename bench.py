@@ -416,6 +416,36 @@ def timed_steps(step, steps, stream, flush, dev):
     return [a.elapsed_time(b) for a, b in ev], clocks.summary()
 
 
+def sampled_plain(q, inst, prm_kw, walks, stream, dev):
+    """The one-walk-per-launch form on a bounded sample of walks: evals/s
+    (2opt moves and tabu iterations, n(n-1)/2 evaluations each)."""
+    import torch
+    n = inst.n
+    prm = q.make_params(walks, launch=q.LAUNCH_PLAIN, **prm_kw)
+    outs = inst.device_outputs(walks, device=dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        inst.search_async(prm, outs, stream=stream)
+        b.record(stream)
+    stream.synchronize()
+    moves = float(outs["iters_done"].sum().item() + outs["descent_moves"].sum().item())
+    return moves * n * (n - 1) / 2 / (a.elapsed_time(b) / 1e3)
+
+
+def sampled_oracle(F, D, walks, **kw):
+    """The oracle (O(1)-update mode, all host cores) on a bounded sample."""
+    import oracle
+    oracle.build()
+    n = F.shape[0]
+    t0 = time.perf_counter()
+    o = oracle.run_walks(F, D, walks, **kw)
+    dt = time.perf_counter() - t0
+    moves = float(o["iters_done"].sum() + o["descent_moves"].sum())
+    return moves * n * (n - 1) / 2 / dt, dt, oracle.num_threads()
+
+
 def other_workloads(args):
     """The remaining workloads, one JSON line each (N = 1)."""
     import torch
@@ -448,6 +478,15 @@ def other_workloads(args):
         ms, clk = timed_steps(graph.replay, args.steps, stream, flush, dev)
         moves = float(outs["iters_done"].sum().item() + outs["descent_moves"].sum().item())
         plan = inst.plan(prm)
+        kw = dict(seed=w["seed"], iters=iters, tenure=w["tenure"], descend=True)
+        plain = sampled_plain(q, inst, kw, 16, stream, dev)
+        cpu, cpu_s, cores = sampled_oracle(w["F"], w["D"], 32, seed=w["seed"], iters=1000,
+                                           tenure=w["tenure"], descend=True)
+        line.update(plain={"value": plain, "unit": "evals/s", "sample": f"16 walks x {iters} "
+                           "iterations, one launch per walk"},
+                    cpu_baseline={"value": cpu, "unit": "evals/s", "cores": cores,
+                                  "kind": "oracle", "sample": "32 walks x (2opt + 1000 "
+                                  f"iterations), {cpu_s:.1f} s wall"})
         line.update(metric=METRIC, value=moves * T / (sum(ms) / 1e3 / args.steps),
                     ms_per_step=sum(ms) / args.steps, steps=args.steps, warmup=args.warmup,
                     dtype="int32" if inst.info["delta_bytes"] == 4 else "int64",
@@ -478,6 +517,27 @@ def other_workloads(args):
         evals = sum(float(it[i].sum()) * insts[i].n * (insts[i].n - 1) / 2
                     for i in range(len(insts)))
         plan = b.plan(prm)
+        # bounded samples: the plain form on 4 walks of 8 instances, the oracle on
+        # 8 walks x 500 iterations of the same 8 instances
+        sample = insts[::64]
+        pl_e = pl_t = cpu_e = cpu_t = 0.0
+        cores = 0
+        for inst_ in sample:
+            with q.Instance(inst_.F, inst_.D, force_int64=True) as one:
+                tn = instances.baseline_tenure(inst_.n)
+                e = sampled_plain(q, one, dict(seed=w["seed"], iters=iters, tenure=tn), 4,
+                                  stream, dev)
+                pl_e += 4 * iters * inst_.n * (inst_.n - 1) / 2
+                pl_t += 4 * iters * inst_.n * (inst_.n - 1) / 2 / e
+            v, dt, cores = sampled_oracle(inst_.F, inst_.D, 8, seed=w["seed"], iters=500,
+                                          tenure=instances.baseline_tenure(inst_.n))
+            cpu_e += v * dt
+            cpu_t += dt
+        line.update(plain={"value": pl_e / pl_t, "unit": "evals/s",
+                           "sample": "4 walks of every 64th instance, one launch per walk"},
+                    cpu_baseline={"value": cpu_e / cpu_t, "unit": "evals/s", "cores": cores,
+                                  "kind": "oracle", "sample": "8 walks x 500 iterations of "
+                                  f"every 64th instance, {cpu_t:.1f} s wall"})
         line.update(metric=METRIC, value=evals / (sum(ms) / 1e3 / args.steps),
                     ms_per_step=sum(ms) / args.steps, steps=args.steps, warmup=args.warmup,
                     dtype="int64", tabu_iters_per_s=float(it.sum()) / (sum(ms) / 1e3 / args.steps),
@@ -645,6 +705,20 @@ def serve(args, q, instances):
         return {"solves_per_s": count / wall, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall}
 
+    # baselines on bounded samples: the same requests one at a time through
+    # qap_search (no overlap), and the plain one-walk-per-launch form
+    t0 = time.perf_counter()
+    for r, p in list(zip(reqs, prms))[:60]:
+        with q.Instance(r.inst.F, r.inst.D) as one:
+            one.search(p)
+    sequential = 60 / (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    for r in reqs[:6]:
+        with q.Instance(r.inst.F, r.inst.D) as one:
+            one.search(q.make_params(32, seed=r.rid, iters=2000,
+                                     tenure=instances.baseline_tenure(r.inst.n),
+                                     launch=q.LAUNCH_PLAIN))
+    plain = 6 / (time.perf_counter() - t0)
     with q.Server(slots=64, mem_bytes=2 << 30) as sv:
         for r in warm:
             sv.wait(sv.submit(r.inst.F, r.inst.D, q.make_params(
@@ -663,6 +737,12 @@ def serve(args, q, instances):
             "capacity_solves_per_s": saturated["solves_per_s"],
             "at_0.8_capacity": {"rate": rate80, **at80},
             "swap_evals_per_s_at_capacity": evals / saturated["wall_s"],
+            "sequential": {"solves_per_s": sequential,
+                           "sample": "first 60 requests one at a time through qap_search"},
+            "plain": {"solves_per_s": plain,
+                      "sample": "first 6 requests, one launch per walk, one at a time"},
+            "capacity_over_sequential": saturated["solves_per_s"] / sequential,
+            "capacity_over_plain": saturated["solves_per_s"] / plain,
             "config": {"workload": f"{count} Poisson requests (2000/s offered), n in [12,256], "
                                    "generators sym uniform / asym uniform / grid",
                        "server": "64 slots, 2 GiB arena, FIFO admission by slot and memory"},
