@@ -117,11 +117,16 @@ KERNEL_SOURCES = ("qap_kernels.cuh", "qap_philox.cuh", "qap_walk_i32_f8.cu",
 
 
 def kernel_source_hash():
+    """Hash of the kernel sources' code: comments and blank lines are left
+    out, so a change of wording does not orphan a profile."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2307_11248_gb300", "csrc")
     for name in KERNEL_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(csrc, name)) as f:
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

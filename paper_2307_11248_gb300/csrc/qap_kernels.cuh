@@ -2,33 +2,36 @@
 //
 // One CTA runs one search walk at a time and loops over walks (persistent
 // form).  Per walk everything lives on chip:
-//   shared memory   F (int8 when every |F| <= 127, else int16) and, for an
+//   shared memory   F (int8 when every difference of two F entries and of
+//                   two D entries fits a byte, else int16) and, for an
 //                   asymmetric flow, F^T; P = D[p][p] (int8) and, for
-//                   asymmetric distances, P^T; the tabu table (int32 per
+//                   asymmetric distances, P^T; the tabu marks (int32 per
 //                   pair); the O(1)-update vectors; two recomputed delta
 //                   rows; g[k] = sum_j F[k][j]P[k][j] + F[j][k]P[j][k]
-//                   (double-buffered); p and the best permutation.
+//                   (double-buffered), or the products M of which g is the
+//                   diagonal (kProductM plans); p and the best permutation.
 //   registers       the delta of every pair the thread owns: a segment of
-//                   at most MAXPT consecutive pairs (u, v) of one row u.
+//                   at most MAXPT consecutive pairs (u, v) of one row u
+//                   (large-n plans keep them in a per-CTA workspace).
 //
 // One tabu iteration, move (r, s) already chosen, has two barriers:
 //   phase X  (reads the pre-move P, called Q below)  one task per index k:
 //            k outside {r, s}: the Eq. 2 deltas of pairs {r, k} and {s, k}
-//            after the move, by dp4a (int8 F) or dp2a (int16 F) dot
-//            products of F / F^T rows with Q / Q^T rows plus O(1)
-//            corrections; the update vectors of k; g'[k] = g[k] - a_k b_k
-//            - c_k e_k.
-//            k in {r, s}: g'[k] by dot products.
+//            after the move, from dot products of F / F^T rows with Q / Q^T
+//            rows (dp4a for int8 F, dp2a for int16 F) or read from M, plus
+//            O(1) corrections; the update vectors of k; g'[k].
+//            k in {r, s}: g'[k].
 //   -- barrier --
 //   phase Y  owners update their deltas: pairs disjoint from {r, s} by
 //            delta += (a_u-a_v)(b_u-b_v) + (c_u-c_v)(e_u-e_v) with
 //              a_x = F[r][x]-F[s][x], b_x = P'[s][x]-P'[r][x],
-//              c_x = F[x][r]-F[x][s], e_x = P'[x][s]-P'[x][r];
-//            pairs touching r or s from the recomputed rows; pair (r, s)
-//            negated; in the same pass each updated delta enters the scan of
-//            the next iteration (tabu / aspiration filter, lowest
-//            (delta, r, s)).  Rows and columns r, s of P (and P^T) are then
-//            exchanged and p[r], p[s] swapped.
+//              c_x = F[x][r]-F[x][s], e_x = P'[x][s]-P'[x][r]
+//            (one dp4a of byte vectors on the int8 path); pairs touching r
+//            or s from the recomputed rows; pair (r, s) negated; each
+//            updated delta enters the scan of the next iteration (tabu /
+//            aspiration filter, lowest (rank, r, s)).  Rows and columns r, s
+//            of P (and P^T) are then exchanged and p[r], p[s] swapped; with
+//            kProductM every thread also brings its share of M up to date.
 //   -- barrier --  (inside the CTA arg-min: warp REDUX, then one round
 //                   through shared memory)
 // Dot products over all j count the j = x and j = k terms; removing them and
