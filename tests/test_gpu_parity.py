@@ -318,8 +318,9 @@ def test_async_search_in_cuda_graph(gpu):
     assert np.array_equal(first["hash"].cpu().numpy().view(np.uint64), o["hash"])
 
 
-@pytest.mark.parametrize("n,sym,products", [(50, False, 1), (100, False, 1), (50, True, 0),
-                                            (170, False, 0)])
+@pytest.mark.parametrize("n,sym,products", [(2, False, 1), (3, False, 1), (5, False, 1),
+                                            (17, False, 1), (50, False, 1), (100, False, 1),
+                                            (50, True, 0), (170, False, 0)])
 def test_phase_x_forms_bit_exact(n, sym, products):
     """Phase X from maintained products (int8 flows, asymmetric, when M fits
     shared memory) and by dot products (the rest): both equal the oracle."""

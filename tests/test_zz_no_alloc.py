@@ -70,3 +70,31 @@ def test_noalloc_rejects_rules_that_need_a_workspace(torch):
                                            b.p_stride, stream.cuda_stream)
             assert e.value.status == q.EUNSUPPORTED
         stream.synchronize()
+
+
+def test_noalloc_products_form_batch(torch):
+    """Asymmetric int8 instances run the products form of phase X; the
+    allocation-free entry point gives the ordinary batch results with it."""
+    Fs, Ds = [], []
+    for k, n in enumerate([12, 50, 33, 64]):
+        F, D = instances.uniform_instance(n, 880 + k, symmetric=False)
+        Fs.append(F)
+        Ds.append(D)
+    W = 3
+    prm = q.make_params(W, seed=5, iters=200, tenure=(4, 12, 0), descend=True)
+    with q.Batch(Fs, Ds) as b:
+        assert b.plan(prm)["products"] == 1
+        stream = torch.cuda.Stream()
+        ref = b.device_outputs(W)
+        b.search_async(prm, ref, stream=stream)
+        stream.synchronize()
+        outs = b.device_outputs(W)
+        q.qap_batch_search_noalloc(b.h, prm, {k: v.data_ptr() for k, v in outs.items()},
+                                   b.p_stride, stream.cuda_stream)
+        stream.synchronize()
+        for k in ref:
+            if k != "best_p":
+                assert torch.equal(outs[k], ref[k]), k
+        for i, F in enumerate(Fs):
+            rows = slice(i * W, (i + 1) * W)
+            assert torch.equal(outs["best_p"][rows, :F.shape[0]], ref["best_p"][rows, :F.shape[0]])
