@@ -619,29 +619,40 @@ __device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, int8_t>& S, cons
 // phase_m_prep:
 //   M'[x][k] = M[x][t(k)] - a_x b_t(k) - c_x e_t(k),  t the transposition
 // (r s): with P'[i][j] = P[t(i)][t(j)], the row-x terms change only at
-// j in {r, s}.  A thread takes 4 consecutive entries of a row (16-byte
-// loads and stores); columns r and s take the other column's entry and
-// word.  Runs beside the owner pass, which does not read M; the next
-// iteration reads Mn after its arg-min barrier.  Columns past n are padding.
+// j in {r, s}.  A thread keeps one group of 4 consecutive columns (16-byte
+// loads and stores) and walks down the rows; in the group holding column r
+// or s, those columns take the other column's entry and word.  Runs beside
+// the owner pass, which does not read M; the next iteration reads Mn after
+// its arg-min barrier.  Columns past n are padding.
 template <int NT>
 __device__ __forceinline__ void phase_m_update(const int32_t* Mc, int32_t* Mn, const int32_t* vw,
                                                int n, int r, int s) {
   const int ldm = ld_m(n), gpr = ldm / 4;
-  const int4* vw4 = reinterpret_cast<const int4*>(vw);
-  for (int item = threadIdx.x; item < n * gpr; item += NT) {
-    const int x = item / gpr, g = item - (item / gpr) * gpr;
-    const int k0 = 4 * g;
+  const int rows = NT / gpr;  // rows per pass: every thread below rows * gpr has a group
+  const int g = threadIdx.x % gpr, x0 = threadIdx.x / gpr;
+  if (x0 >= rows) return;
+  const int k0 = 4 * g;
+  int4 w = reinterpret_cast<const int4*>(vw)[g];
+  const int jr = r - k0, js = s - k0;  // positions of columns r, s in this group
+  const bool hr = (unsigned)jr < 4u, hs = (unsigned)js < 4u;
+  if (hr | hs) {
+    const int wr = vw[r], ws = vw[s];
+    if (jr == 0 || js == 0) w.x = jr == 0 ? ws : wr;
+    if (jr == 1 || js == 1) w.y = jr == 1 ? ws : wr;
+    if (jr == 2 || js == 2) w.z = jr == 2 ? ws : wr;
+    if (jr == 3 || js == 3) w.w = jr == 3 ? ws : wr;
+  }
+  for (int x = x0; x < n; x += rows) {
     // bytes (a_x, c_x, 0, 0) against (b, e, a, c) of each column
     const int ux = (int)__byte_perm((uint32_t)vw[x], 0u, 0x4432u);
-    int4 m = reinterpret_cast<const int4*>(Mc + x * ldm)[g];
-    int4 w = vw4[g];
-    if ((unsigned)(r - k0) < 4u || (unsigned)(s - k0) < 4u) {
-      const int msr = Mc[x * ldm + s], mrs = Mc[x * ldm + r];
-      const int wsr = vw[s], wrs = vw[r];
-      if (k0 + 0 == r) { m.x = msr; w.x = wsr; } else if (k0 + 0 == s) { m.x = mrs; w.x = wrs; }
-      if (k0 + 1 == r) { m.y = msr; w.y = wsr; } else if (k0 + 1 == s) { m.y = mrs; w.y = wrs; }
-      if (k0 + 2 == r) { m.z = msr; w.z = wsr; } else if (k0 + 2 == s) { m.z = mrs; w.z = wrs; }
-      if (k0 + 3 == r) { m.w = msr; w.w = wsr; } else if (k0 + 3 == s) { m.w = mrs; w.w = wrs; }
+    const int32_t* Mx = Mc + x * ldm;
+    int4 m = reinterpret_cast<const int4*>(Mx)[g];
+    if (hr | hs) {
+      const int mr = Mx[r], ms = Mx[s];
+      if (jr == 0 || js == 0) m.x = jr == 0 ? ms : mr;
+      if (jr == 1 || js == 1) m.y = jr == 1 ? ms : mr;
+      if (jr == 2 || js == 2) m.z = jr == 2 ? ms : mr;
+      if (jr == 3 || js == 3) m.w = jr == 3 ? ms : mr;
     }
     m.x -= __dp4a(ux, w.x, 0);
     m.y -= __dp4a(ux, w.y, 0);
