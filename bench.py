@@ -529,13 +529,13 @@ def other_workloads(args):
         cores = 0
         for inst_ in sample:
             with q.Instance(inst_.F, inst_.D, force_int64=True) as one:
-                tn = instances.baseline_tenure(inst_.n)
+                tn = instances.periodic_tenure(inst_.n)
                 e = sampled_plain(q, one, dict(seed=w["seed"], iters=iters, tenure=tn), 4,
                                   stream, dev)
                 pl_e += 4 * iters * inst_.n * (inst_.n - 1) / 2
                 pl_t += 4 * iters * inst_.n * (inst_.n - 1) / 2 / e
             v, dt, cores = sampled_oracle(inst_.F, inst_.D, 8, seed=w["seed"], iters=500,
-                                          tenure=instances.baseline_tenure(inst_.n))
+                                          tenure=instances.periodic_tenure(inst_.n))
             cpu_e += v * dt
             cpu_t += dt
         line.update(plain={"value": pl_e / pl_t, "unit": "evals/s",
@@ -634,7 +634,7 @@ def sweep(args, q, instances, stream, dev):
                                           instances.workload_asym50()["D"]), False),
                               ("lognormal100", lognormal, True)):
         n = F.shape[0]
-        tn = instances.baseline_tenure(n)
+        tn = instances.periodic_tenure(n)
         inst = q.Instance(F, D, force_int64=f64)
         run(inst, 64, 100, 1, tn)  # warm-up
         rows = []
@@ -688,7 +688,7 @@ def serve(args, q, instances):
     at the offered 2000 req/s and at 0.8x the measured capacity."""
     count = args.requests
     reqs = instances.poisson_requests(count, seed=4, rate_per_s=2000.0)
-    prms = [q.make_params(32, seed=r.rid, iters=2000, tenure=instances.baseline_tenure(r.inst.n))
+    prms = [q.make_params(32, seed=r.rid, iters=2000, tenure=instances.periodic_tenure(r.inst.n))
             for r in reqs]
     warm = instances.poisson_requests(20, seed=99)
 
@@ -721,13 +721,13 @@ def serve(args, q, instances):
     for r in reqs[:6]:
         with q.Instance(r.inst.F, r.inst.D) as one:
             one.search(q.make_params(32, seed=r.rid, iters=2000,
-                                     tenure=instances.baseline_tenure(r.inst.n),
+                                     tenure=instances.periodic_tenure(r.inst.n),
                                      launch=q.LAUNCH_PLAIN))
     plain = 6 / (time.perf_counter() - t0)
     with q.Server(slots=64, mem_bytes=2 << 30) as sv:
         for r in warm:
             sv.wait(sv.submit(r.inst.F, r.inst.D, q.make_params(
-                32, seed=r.rid, iters=200, tenure=instances.baseline_tenure(r.inst.n))))
+                32, seed=r.rid, iters=200, tenure=instances.periodic_tenure(r.inst.n))))
         run(0, sv)                        # grows every slot's pinned buffers and the arena
         saturated = run(0, sv)            # all at once: capacity
         offered = run(2000.0, sv)         # the offered Poisson rate

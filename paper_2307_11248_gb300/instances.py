@@ -160,7 +160,7 @@ def poisson_requests(count: int, seed: int, rate_per_s: float = 2000.0, nmin: in
     return reqs
 
 
-def baseline_tenure(n: int):
+def periodic_tenure(n: int):
     """Tenure range [floor(0.9 n), ceil(1.1 n)] redrawn every 2n iterations."""
     return (max(1, (9 * n) // 10), (11 * n + 9) // 10, 2 * n)
 
@@ -186,13 +186,13 @@ def workload_sym12():
 def workload_asym50():
     """n=50 asymmetric uniform [0,99], tabu 256 walks x 5000 iterations."""
     F, D = uniform_instance(50, 1, False)
-    return dict(F=F, D=D, walks=256, iters=5000, tenure=baseline_tenure(50), seed=1002)
+    return dict(F=F, D=D, walks=256, iters=5000, tenure=periodic_tenure(50), seed=1002)
 
 
 def workload_grid100():
     """n=100 grid instance, 2opt then tabu, 1024 walks x 10000 iterations."""
     F, D = grid_instance(100, 2)
-    return dict(F=F, D=D, walks=1024, iters=10000, tenure=baseline_tenure(100), seed=1003)
+    return dict(F=F, D=D, walks=1024, iters=10000, tenure=periodic_tenure(100), seed=1003)
 
 
 def workload_batch512():

@@ -70,7 +70,7 @@ def test_tenure_per_n_matches_each_instance_rule():
         g = b.search(q.make_params(W, seed=8, iters=300, tenure=(90, 110, 200), tenure_per_n=True))
     for i in range(3):
         check_instance(g, i, W, Fs[i], Ds[i], seed=8, iters=300,
-                       tenure=instances.baseline_tenure(Fs[i].shape[0]))
+                       tenure=instances.periodic_tenure(Fs[i].shape[0]))
 
 
 def test_batch_equals_single_instance_searches():
@@ -137,7 +137,7 @@ def test_full_batch512_sampled_walks():
         inst = insts[i]
         rows = [int(i * W + k) for k in (0, W - 1)]
         o = oracle.run_walks(inst.F, inst.D, 2, seed=w["seed"], iters=iters,
-                             tenure=instances.baseline_tenure(inst.n), walk_ids=np.array([0, W - 1]))
+                             tenure=instances.periodic_tenure(inst.n), walk_ids=np.array([0, W - 1]))
         for k in FIELDS:
             assert np.array_equal(g[k][rows].astype(np.int64), o[k].astype(np.int64)), (i, k)
         assert np.array_equal(g["best_p"][rows, :inst.n], o["best_p"])
@@ -162,7 +162,7 @@ def test_batch_with_large_instances_uses_workspace():
         g = b.search(prm)
     for i in range(len(Fs)):
         check_instance(g, i, W, Fs[i], Ds[i], seed=4, iters=50,
-                       tenure=instances.baseline_tenure(Fs[i].shape[0]))
+                       tenure=instances.periodic_tenure(Fs[i].shape[0]))
 
 
 def test_size_classes_match_single_instance_searches():

@@ -152,7 +152,7 @@ def test_grid100_full_iterations_sampled_walks():
 def test_lognormal_batch_instances_int64(k):
     inst = instances.batch_instances(16, 3)[k]
     n = inst.n
-    tn = instances.baseline_tenure(n)
+    tn = instances.periodic_tenure(n)
     g, o, info = run_both(inst.F, inst.D, 6, seed=1004, iters=400, tenure=tn, force_int64=True)
     assert info["delta_bytes"] == 8
     assert_same(g, o)
@@ -180,7 +180,7 @@ def test_large_n_global_workspace(n, sym, descend):
     n = 256 also reads F from global memory."""
     F, D = instances.uniform_instance(n, 300 + n, symmetric=sym)
     iters = 60
-    tn = instances.baseline_tenure(n)
+    tn = instances.periodic_tenure(n)
     g, o, info = run_both(F, D, 3, seed=19, iters=iters, tenure=tn, descend=descend,
                           max_descent=40)
     assert_same(g, o)

@@ -25,7 +25,7 @@ def gpu():
 
 
 def request_params(n, rid, iters=120, walks=8):
-    return q.make_params(walks, seed=rid, iters=iters, tenure=instances.baseline_tenure(n))
+    return q.make_params(walks, seed=rid, iters=iters, tenure=instances.periodic_tenure(n))
 
 
 def alone(F, D, prm):
@@ -48,7 +48,7 @@ def test_requests_equal_oracle_and_alone():
             prm = request_params(n, r.rid)
             assert same(res, alone(r.inst.F, r.inst.D, prm)), (r.rid, n)
             o = oracle.run_walks(r.inst.F, r.inst.D, prm.starts, seed=r.rid, iters=prm.iters,
-                                 tenure=instances.baseline_tenure(n))
+                                 tenure=instances.periodic_tenure(n))
             for k in FIELDS:
                 assert np.array_equal(res[k].astype(np.int64), o[k].astype(np.int64)), (r.rid, k)
             assert times["total_us"] >= times["device_us"] > 0

@@ -78,7 +78,7 @@ def test_paper_tenure_int64_lognormal():
 def test_frequency_memory_single_instance(tenure):
     n = 50
     F, D = instances.uniform_instance(n, 11, symmetric=False)
-    tn = instances.paper_tenure(n) if tenure == "paper" else instances.baseline_tenure(n)
+    tn = instances.paper_tenure(n) if tenure == "paper" else instances.periodic_tenure(n)
     W, iters = 5, 500
     with q.Instance(F, D) as inst:
         g = inst.search(q.make_params(W, seed=21, iters=iters, tenure=tn), freq=True)
