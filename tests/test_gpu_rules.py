@@ -182,3 +182,24 @@ def test_bad_rules_are_rejected():
             with pytest.raises(q.QapError) as e:
                 inst.search(q.make_params(1, seed=1, iters=5, tenure=(1, 2, 0), **kw))
             assert e.value.status == q.EINVAL
+
+
+def test_rules_int64_flows_in_global_memory():
+    """Large n with int16 flows and int64 deltas: the workspace plan with F in
+    global memory, under the unit-location criterion and the penalty."""
+    F, D = instances.lognormal_instance(230, 31, symmetric=False)
+    tn = (20, 60, 0)
+    prm = q.make_params(2, seed=3, iters=60, tenure=tn, criterion=q.TABU_UNIT_LOC,
+                        freq_penalty=3)
+    with q.Instance(F, D, force_int64=True) as inst:
+        pl = inst.plan(prm)
+        assert pl["workspace"] == 1 and pl["products"] == 0
+        g = inst.search(prm, freq=True)
+    o = oracle.run_walks(F, D, 2, seed=3, iters=60, tenure=tn, criterion=q.TABU_UNIT_LOC,
+                         penalty=3)
+    check(g, o)
+    for w in range(2):
+        p0 = oracle.start_perm(3, w, 230)
+        *_, fq = oracle.tabu(F, D, p0, 60, *tn, True, 3, w, want_freq=True,
+                             criterion=q.TABU_UNIT_LOC, penalty=3)
+        assert np.array_equal(g["freq"][w], fq)
