@@ -14,6 +14,9 @@ namespace qapk {
     case 512040: return K<DT, FE, 512, 4, 0>;                    \
     case 512080: return K<DT, FE, 512, 8, 0>;                    \
     case 512120: return K<DT, FE, 512, 12, 0>;                   \
+    case 512160: return K<DT, FE, 512, 16, 0>;                   \
+    case 512200: return K<DT, FE, 512, 20, 0>;                   \
+    case 512240: return K<DT, FE, 512, 24, 0>;                   \
     case 1024080: return K<DT, FE, 1024, 8, 0>;                  \
     case 1024120: return K<DT, FE, 1024, 12, 0>;                 \
     case 1024160: return K<DT, FE, 1024, 16, 0>;                 \

@@ -14,6 +14,7 @@ namespace qapk {
     case 512044: return K<DT, FE, 512, 4, kProductM>;            \
     case 512084: return K<DT, FE, 512, 8, kProductM>;            \
     case 512124: return K<DT, FE, 512, 12, kProductM>;           \
+    case 512164: return K<DT, FE, 512, 16, kProductM>;           \
     case 1024084: return K<DT, FE, 1024, 8, kProductM>;          \
     case 1024124: return K<DT, FE, 1024, 12, kProductM>;         \
     default: return nullptr;                                     \

@@ -68,8 +68,9 @@ inline constexpr Plan kLargePlan = {1024, 40, qapk::kGlobalDelta};
 // fewest threads that fit at all; for a given thread count the fewest slots
 // that fit.
 inline constexpr Plan kPlans[] = {{128, 4, 0},   {128, 12, 0},  {256, 6, 0},   {256, 8, 0},
-                       {512, 4, 0},   {512, 8, 0},   {512, 12, 0},  {1024, 8, 0},
-                       {1024, 12, 0}, {1024, 16, 0}, {1024, 20, 0}};
+                       {512, 4, 0},   {512, 8, 0},   {512, 12, 0},  {512, 16, 0},
+                       {512, 20, 0},  {512, 24, 0},  {1024, 8, 0},  {1024, 12, 0},
+                       {1024, 16, 0}, {1024, 20, 0}};
 
 inline bool plan_for(int n, int nt, Plan* out) {
   for (const Plan& p : kPlans)
@@ -205,7 +206,7 @@ inline int plan_smem(const Plan& p, const DevInstance* d, int count, int fbytes,
 
 // Register plans compiled with the maintained products M (int8 flows).
 inline bool has_product_form(const Plan& p) {
-  return p.store == 0 && (p.nt < 1024 || p.maxpt <= 12);
+  return p.store == 0 && (p.nt == 1024 ? p.maxpt <= 12 : p.nt < 512 || p.maxpt <= 16);
 }
 
 // The products form of a register plan when the flows are int8, an
