@@ -110,10 +110,9 @@ class ClockSampler:
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
-# the sources that make the int8-flow walk kernels (the profiled one is the
-# products form, qap_walk_i32_f8m.cu)
-KERNEL_SOURCES = ("qap_kernels.cuh", "qap_philox.cuh", "qap_walk_i32_f8.cu",
-                  "qap_walk_i32_f8m.cu")
+# the sources of the kernels' code (the qap_walk_* / qap_batch_* units only
+# list which template instances exist)
+KERNEL_SOURCES = ("qap_kernels.cuh", "qap_philox.cuh")
 
 
 def kernel_source_hash():
