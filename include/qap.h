@@ -261,6 +261,17 @@ qap_status qap_tabu(qap_ctx* ctx, int32_t starts, int32_t iters, qap_tenure tenu
                     int32_t aspiration, uint64_t seed, int32_t* best_p, int64_t* best_cost,
                     int32_t* best_iter, int32_t* status);
 
+/* The host's reduction over walks (Sections 4.2 and 4.4: each walk returns
+ * its best solution, the minimum is taken on the CPU): for each of `groups`
+ * consecutive groups of `walks` entries of best_cost (host pointer, groups x
+ * walks), the index within the group of the lowest cost, ties to the lowest
+ * walk index, into index[groups] (host).  groups = 1 for one instance; the
+ * instance count for a batch search (rows i * starts + k).  Runs on the
+ * host; no GPU call.  Errors: QAP_EINVAL on null pointers, walks < 1 or
+ * groups < 0. */
+qap_status qap_best_walks(const int64_t* best_cost, int32_t groups, int32_t walks,
+                          int32_t* index);
+
 /* ------------------------------------------------------------------------
  * Many instances of uneven n in one persistent launch (the walks of every
  * instance are independent searches, Sections 4.2 and 4.4).  CTAs take

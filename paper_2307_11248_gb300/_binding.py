@@ -136,6 +136,8 @@ def lib():
             L.qap_batch_plan.argtypes = [vp, ctypes.POINTER(SearchParams),
                                          ctypes.POINTER(PlanInfo)]
             L.qap_batch_plan.restype = st
+            L.qap_best_walks.argtypes = [vp, i32, i32, vp]
+            L.qap_best_walks.restype = st
             L.qap_batch_autotune.argtypes = [vp, ctypes.POINTER(SearchParams), i32,
                                              ctypes.POINTER(TuneResult), i32,
                                              ctypes.POINTER(i32)]
@@ -278,6 +280,18 @@ def qap_2opt(h, starts, seed, max_iters=-1, n=None):
     _check(lib().qap_2opt(h, starts, int(seed), max_iters, _ptr(best_p), _ptr(best_cost),
                           _ptr(moves)), "qap_2opt")
     return best_p, best_cost, moves
+
+
+def qap_best_walks(best_cost, walks):
+    """Index of the best walk of each group of `walks` consecutive entries
+    (lowest cost, ties to the lowest walk index), through the C-ABI."""
+    c = np.ascontiguousarray(best_cost, dtype=np.int64).reshape(-1)
+    if walks < 1 or c.size % walks:
+        raise QapError(EINVAL, "qap_best_walks")
+    groups = c.size // walks
+    idx = np.zeros(groups, dtype=np.int32)
+    _check(lib().qap_best_walks(_ptr(c), groups, int(walks), _ptr(idx)), "qap_best_walks")
+    return idx
 
 
 def qap_tabu(h, starts, iters, tenure, aspiration, seed, n=None):

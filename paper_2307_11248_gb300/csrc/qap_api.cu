@@ -469,6 +469,19 @@ qap_status qap_2opt(qap_ctx* ctx, int32_t starts, uint64_t seed, int32_t max_ite
   return qap_search(ctx, &p, nullptr, &o);
 }
 
+qap_status qap_best_walks(const int64_t* best_cost, int32_t groups, int32_t walks,
+                          int32_t* index) {
+  if (groups < 0 || walks < 1 || (groups > 0 && (!best_cost || !index))) return QAP_EINVAL;
+  for (int32_t g = 0; g < groups; ++g) {
+    const int64_t* c = best_cost + (size_t)g * walks;
+    int32_t k = 0;
+    for (int32_t w = 1; w < walks; ++w)
+      if (c[w] < c[k]) k = w;
+    index[g] = k;
+  }
+  return QAP_OK;
+}
+
 qap_status qap_tabu(qap_ctx* ctx, int32_t starts, int32_t iters, qap_tenure tenure,
                     int32_t aspiration, uint64_t seed, int32_t* best_p, int64_t* best_cost,
                     int32_t* best_iter, int32_t* status) {

@@ -54,3 +54,19 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
     with pytest.raises(q.QapError) as e:
         q.qap_create(np.zeros((300, 300)), np.zeros((300, 300)))
     assert e.value.status == q.EUNSUPPORTED
+
+
+def test_best_walks_reduction_on_the_host():
+    """The host reduction over walks (lowest cost, ties to the lowest walk
+    index) runs without a GPU and agrees with a first-occurrence arg-min."""
+    import numpy as np
+    import paper_2307_11248_gb300 as q
+    rng = np.random.default_rng(3)
+    c = rng.integers(0, 5, size=(7, 9)).astype(np.int64)  # many ties
+    idx = q.qap_best_walks(c, 9)
+    assert idx.tolist() == np.argmin(c, axis=1).tolist()
+    assert q.qap_best_walks(np.array([5, 5, 5]), 3).tolist() == [0]
+    assert q.qap_best_walks(np.zeros(0, dtype=np.int64), 4).tolist() == []
+    with pytest.raises(q.QapError) as e:
+        q.qap_best_walks(c, 0)
+    assert e.value.status == q.EINVAL

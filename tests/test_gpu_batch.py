@@ -226,3 +226,20 @@ def test_autotune_rejects_fixed_thread_counts():
         with pytest.raises(q.QapError) as e:
             b.autotune(q.make_params(2, seed=1, iters=10, tenure=(1, 2, 0), threads_per_walk=256))
         assert e.value.status == q.EINVAL
+
+
+def test_best_walk_per_instance_matches_the_oracle():
+    """The host reduction over walks (a walk's best, then the minimum over
+    walks, ties to the lowest walk) on a batch search's outputs."""
+    insts = instances.batch_instances(5, 17)
+    W = 6
+    tn = (5, 15, 30)
+    with q.Batch([i.F for i in insts], [i.D for i in insts], force_int64=True) as b:
+        g = b.search(q.make_params(W, seed=41, iters=150, tenure=tn))
+    idx = q.qap_best_walks(g["best_cost"], W)
+    for i, inst in enumerate(insts):
+        o = oracle.run_walks(inst.F, inst.D, W, seed=41, iters=150, tenure=tn)
+        k = int(np.argmin(o["best_cost"]))
+        assert idx[i] == k
+        assert g["best_cost"][i * W + k] == o["best_cost"][k]
+        assert np.array_equal(g["best_p"][i * W + k, :inst.n], o["best_p"][k])
