@@ -977,16 +977,23 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         const DT gu = su == r ? gr : gs;
         bd = DeltaMax<DT>::v;
         bk = kNoMove;
+        // slen differs between the lanes: with few int32 slots they are
+        // predicated off (measured faster at 6 slots), otherwise the loop
+        // exits early (measured faster at 12 to 24 slots and with int64)
 #pragma unroll
         for (int i = 0; i < MAXPT; ++i) {
-          if (i >= slen) break;
-          const int v = sv + i;
+          if constexpr (MAXPT > 8 || sizeof(DT) == 8) {
+            if (i >= slen) break;
+          }
+          const bool valid = i < slen;
+          const int v = valid ? sv + i : sv;
           const bool isrs = (su == r) & (i == is);
-          const DT d = isrs ? nrs : S.R[ubase + v] - gu;
+          const DT dn = isrs ? nrs : S.R[ubase + v] - gu;
+          const DT d = valid ? dn : dl.get(i);
           dl.set(i, d);
           const int tb = isrs ? stamp : S.tabu[i * NT + tid];
           const DT sc = rank(d, v);
-          if ((tb <= tlim || d < lim) && sc < bd) {
+          if (valid && (tb <= tlim || d < lim) && sc < bd) {
             bd = sc;
             bk = ukey | (uint32_t)v;
           }
