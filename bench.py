@@ -483,14 +483,16 @@ def other_workloads(args):
         moves = float(outs["iters_done"].sum().item() + outs["descent_moves"].sum().item())
         plan = inst.plan(prm)
         kw = dict(seed=w["seed"], iters=iters, tenure=w["tenure"], descend=True)
-        plain = sampled_plain(q, inst, kw, 16, stream, dev)
-        cpu, cpu_s, cores = sampled_oracle(w["F"], w["D"], 32, seed=w["seed"], iters=1000,
-                                           tenure=w["tenure"], descend=True)
-        line.update(plain={"value": plain, "unit": "evals/s", "sample": f"16 walks x {iters} "
-                           "iterations, one launch per walk"},
-                    cpu_baseline={"value": cpu, "unit": "evals/s", "cores": cores,
-                                  "kind": "oracle", "sample": "32 walks x (2opt + 1000 "
-                                  f"iterations), {cpu_s:.1f} s wall"})
+        if not args.no_plain:
+            plain = sampled_plain(q, inst, kw, 16, stream, dev)
+            line.update(plain={"value": plain, "unit": "evals/s", "sample": f"16 walks x "
+                               f"{iters} iterations, one launch per walk"})
+        if not args.no_cpu:
+            cpu, cpu_s, cores = sampled_oracle(w["F"], w["D"], 32, seed=w["seed"], iters=1000,
+                                               tenure=w["tenure"], descend=True)
+            line.update(cpu_baseline={"value": cpu, "unit": "evals/s", "cores": cores,
+                                      "kind": "oracle", "sample": "32 walks x (2opt + 1000 "
+                                      f"iterations), {cpu_s:.1f} s wall"})
         line.update(metric=METRIC, value=moves * T / (sum(ms) / 1e3 / args.steps),
                     ms_per_step=sum(ms) / args.steps, steps=args.steps, warmup=args.warmup,
                     dtype="int32" if inst.info["delta_bytes"] == 4 else "int64",
@@ -527,21 +529,26 @@ def other_workloads(args):
         pl_e = pl_t = cpu_e = cpu_t = 0.0
         cores = 0
         for inst_ in sample:
-            with q.Instance(inst_.F, inst_.D, force_int64=True) as one:
-                tn = instances.periodic_tenure(inst_.n)
-                e = sampled_plain(q, one, dict(seed=w["seed"], iters=iters, tenure=tn), 4,
-                                  stream, dev)
-                pl_e += 4 * iters * inst_.n * (inst_.n - 1) / 2
-                pl_t += 4 * iters * inst_.n * (inst_.n - 1) / 2 / e
-            v, dt, cores = sampled_oracle(inst_.F, inst_.D, 8, seed=w["seed"], iters=500,
-                                          tenure=instances.periodic_tenure(inst_.n))
-            cpu_e += v * dt
-            cpu_t += dt
-        line.update(plain={"value": pl_e / pl_t, "unit": "evals/s",
-                           "sample": "4 walks of every 64th instance, one launch per walk"},
-                    cpu_baseline={"value": cpu_e / cpu_t, "unit": "evals/s", "cores": cores,
-                                  "kind": "oracle", "sample": "8 walks x 500 iterations of "
-                                  f"every 64th instance, {cpu_t:.1f} s wall"})
+            if not args.no_plain:
+                with q.Instance(inst_.F, inst_.D, force_int64=True) as one:
+                    tn = instances.periodic_tenure(inst_.n)
+                    e = sampled_plain(q, one, dict(seed=w["seed"], iters=iters, tenure=tn), 4,
+                                      stream, dev)
+                    pl_e += 4 * iters * inst_.n * (inst_.n - 1) / 2
+                    pl_t += 4 * iters * inst_.n * (inst_.n - 1) / 2 / e
+            if not args.no_cpu:
+                v, dt, cores = sampled_oracle(inst_.F, inst_.D, 8, seed=w["seed"], iters=500,
+                                              tenure=instances.periodic_tenure(inst_.n))
+                cpu_e += v * dt
+                cpu_t += dt
+        if not args.no_plain:
+            line.update(plain={"value": pl_e / pl_t, "unit": "evals/s",
+                               "sample": "4 walks of every 64th instance, one launch per walk"})
+        if not args.no_cpu:
+            line.update(cpu_baseline={"value": cpu_e / cpu_t, "unit": "evals/s",
+                                      "cores": cores, "kind": "oracle",
+                                      "sample": "8 walks x 500 iterations of every 64th "
+                                      f"instance, {cpu_t:.1f} s wall"})
         line.update(metric=METRIC, value=evals / (sum(ms) / 1e3 / args.steps),
                     ms_per_step=sum(ms) / args.steps, steps=args.steps, warmup=args.warmup,
                     dtype="int64", tabu_iters_per_s=float(it.sum()) / (sum(ms) / 1e3 / args.steps),

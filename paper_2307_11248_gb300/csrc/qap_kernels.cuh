@@ -713,24 +713,32 @@ __device__ __forceinline__ void swap_rs(int8_t* P, int8_t* Pt, int32_t* perm, in
 // ---------------------------------------------------------------------------
 constexpr int min_blocks(int nt) { return nt <= 128 ? 4 : nt <= 256 ? 2 : 1; }
 
-// Pairs are handed out as row segments: row u holds the pairs (u, v), v > u;
-// it is cut into segments of at most MAXPT consecutive v, and thread t owns
-// segment t in row-major order.  The host checks that every segment has a
-// thread.
+// Pairs are handed out by rows: row u holds the pairs (u, v), v > u, and
+// gets c_u = ceil((n - 1 - u) / MAXPT) threads, in row-major order.  Its
+// thread j owns either the run v = u + 1 + j MAXPT + i (contiguous), or
+// v = u + 1 + j + i c_u (interleaved: at each slot the threads of a row read
+// consecutive entries of the per-index arrays, free of shared-memory bank
+// conflicts for 16-byte entries), i = 0, 1, ... (at most MAXPT).  The host
+// checks that every row segment (one per thread) has a thread.
 __host__ __device__ inline int row_segments(int n, int maxpt) {
   int nseg = 0;
   for (int u = 0; u < n - 1; ++u) nseg += (n - 1 - u + maxpt - 1) / maxpt;
   return nseg;
 }
 
+// The interleaved layout where it measured faster: 16-byte per-index entries
+// (int16 flows), up to 512 threads (at 1024 the extra registers spill).
+template <typename FE, int NT>
+__host__ __device__ constexpr bool interleaved() { return sizeof(FE) == 2 && NT <= 512; }
+
 struct Segment {
-  int su, sv, slen;  // pairs (su, sv + i), i < slen
-  int wlen;          // longest segment in the warp
+  int su, sv, sk, slen;  // pairs (su, sv + i sk), i < slen
+  int wlen;              // most slots in the warp
 };
 
-template <int MAXPT>
+template <int MAXPT, bool INTERLEAVE>
 __device__ __forceinline__ Segment make_segment(int n) {
-  Segment g{0, 1, 0, 0};
+  Segment g{0, 1, 1, 0, 0};
   const int tid = threadIdx.x;
   int t0 = 0;
   for (int u = 0; u < n - 1; ++u) {
@@ -739,8 +747,14 @@ __device__ __forceinline__ Segment make_segment(int n) {
     if (tid >= t0 && tid < t0 + ns) {
       const int j = tid - t0;
       g.su = u;
-      g.sv = u + 1 + j * MAXPT;
-      g.slen = min(MAXPT, len - j * MAXPT);
+      if (INTERLEAVE) {
+        g.sv = u + 1 + j;
+        g.sk = ns;
+        g.slen = (len - j + ns - 1) / ns;  // at most MAXPT
+      } else {
+        g.sv = u + 1 + j * MAXPT;
+        g.slen = min(MAXPT, len - j * MAXPT);
+      }
     }
     t0 += ns;
   }
@@ -838,8 +852,18 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   const int n = I.n, ldF = I.ldF, ldP = I.ldP, tid = threadIdx.x, G = I.group;
   const bool sym = I.symF && I.symD;
   const bool warp0 = tid < 32;
+  constexpr bool kInterleave = interleaved<FE, NT>();
   const int su = seg.su, sv = seg.sv, slen = seg.slen, wlen = seg.wlen;
+  const int sk = kInterleave ? seg.sk : 1;
+  const int seg_sv = sv, seg_sk = sk;
   const uint32_t ukey = (uint32_t)su << 8;
+  // slot of the pair (su, x), or -1 when this thread does not hold it
+  auto slot_of = [&](int x) {
+    const int d = x - sv;
+    if (d < 0) return -1;
+    const int q = d / sk;
+    return q * sk == d && q < slen ? q : -1;
+  };
 
   // Start permutation: given, or Fisher-Yates on stream 0.
   if (start) {
@@ -891,7 +915,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   constexpr bool kSplitPass = !(STORE & kGlobalDelta);
 #pragma unroll
   for (int i = 0; i < MAXPT; ++i) {
-    dl.set(i, i < slen ? delta_serial<DT, FE>(S, n, ldF, ldP, sym, su, sv + i)
+    dl.set(i, i < slen ? delta_serial<DT, FE>(S, n, ldF, ldP, sym, su, sv + i * sk)
                        : DeltaMax<DT>::v);
     S.tabu[i * NT + tid] = 0;
   }
@@ -911,8 +935,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   // again.
   // Tables of the other tabu criteria and of the frequency penalty, in the
   // CTA's workspace: loc_until[unit][location] (n x n), unit_until[unit] (n)
-  // and applied[r][s] (n x n, the penalty's counts, row-major so that a
-  // segment's are contiguous).  Addressed from the launch arguments when
+  // and applied[r][s] (n x n, the penalty's counts, row-major).  Addressed from the launch arguments when
   // used so that they hold no registers in the paper's own search.
   auto rule_tables = [&]() { return reinterpret_cast<int32_t*>(ws + a.rws_off); };
   auto applied = [&]() { return rule_tables() + n * n + n; };
@@ -929,7 +952,6 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     const typename VO::U uu = VO::prep(vec[su]);
     const DT gr = gn[r], gs = gn[s];
     const bool tu = (su == r) | (su == s);        // every pair of the segment touches
-    const int ir = r - sv, is = s - sv;           // slots of (su, r), (su, s) if held
     const DT xr = S.R[su] - gr, xs = S.R[n + su] - gs;
     // admissible: not tabu (mark <= nit), or aspiring (ncur + d < nbest,
     // i.e. d < nbest - ncur, clamped where no delta can reach it)
@@ -947,21 +969,36 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     };
     bd = DeltaMax<DT>::v;
     bk = kNoMove;
+    int irs = -1;  // interleaved: slot of the pair (r, s), where held
+    // interleaved: the slots' v are recomputed in each pass rather than held
+    // across the iterations (which costs MAXPT registers)
+    int sv = seg_sv, sk = seg_sk;
+    if constexpr (kInterleave) asm volatile("" : "+r"(sv), "+r"(sk));
+    const int ir = r - sv, is = s - sv;  // contiguous: slots of (su, r), (su, s) if held
+    auto at_r = [&](int i) {
+      if constexpr (kInterleave) return sv + i * sk == r;
+      else return i == ir;
+    };
+    auto at_s = [&](int i) {
+      if constexpr (kInterleave) return sv + i * sk == s;
+      else return i == is;
+    };
     if constexpr (kSplitPass) {
       // the pair (r, s) itself only changes sign
       DT nrs = 0;
       if (su == r) {
 #pragma unroll
         for (int i = 0; i < MAXPT; ++i)
-          if (i == is) nrs = -dl.get(i);
+          if (at_s(i)) nrs = -dl.get(i);
       }
 #pragma unroll
       for (int i = 0; i < MAXPT; ++i) {
         if (i >= wlen) break;
         const bool valid = i < slen;
-        const int v = valid ? sv + i : sv;
+        const int vi = sv + i * sk;
+        const int v = valid ? vi : sv;
         DT d = VO::update(uu, vec[v], dl.get(i));
-        d = i == ir ? xr : i == is ? xs : d;
+        d = at_r(i) ? xr : at_s(i) ? xs : d;
         dl.set(i, d);
         const int tb = S.tabu[i * NT + tid];
         const DT sc = rank(d, v);
@@ -986,11 +1023,15 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
             if (i >= slen) break;
           }
           const bool valid = i < slen;
-          const int v = valid ? sv + i : sv;
-          const bool isrs = (su == r) & (i == is);
+          const int vi = sv + i * sk;
+          const int v = valid ? vi : sv;
+          const bool isrs = (su == r) & at_s(i);
           const DT dn = isrs ? nrs : S.R[ubase + v] - gu;
           const DT d = valid ? dn : dl.get(i);
           dl.set(i, d);
+          if constexpr (kInterleave) {
+            if (valid & isrs) irs = i;
+          }
           const int tb = isrs ? stamp : S.tabu[i * NT + tid];
           const DT sc = rank(d, v);
           if (valid && (tb <= tlim || d < lim) && sc < bd) {
@@ -1008,17 +1049,21 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       for (int i = 0; i < MAXPT; ++i) {
         if (i >= wlen) break;
         const bool valid = i < slen;
-        const int v = valid ? sv + i : sv;
-        const bool tvr = i == ir, tv = tvr | (i == is);
+        const int vi = sv + i * sk;
+        const int v = valid ? vi : sv;
+        const bool tvr = at_r(i), tv = tvr | at_s(i);
         const int idx = tu ? ubase + v : (tvr ? 0 : n) + su;  // in range for any v, su
         const DT rv = S.R[idx];
         const int tbl = S.tabu[i * NT + tid];
         const DT gx = tu ? gu : (tvr ? gr : gs);
         DT d = dl.get(i);
         const DT o1 = VO::update(uu, vec[v], d);
-        const bool isrs = (su == r) & (i == is);
+        const bool isrs = (su == r) & at_s(i);
         d = isrs ? -d : (tu | tv) ? rv - gx : o1;
         dl.set(i, d);
+        if constexpr (kInterleave) {
+          if (valid & isrs) irs = i;
+        }
         const int tb = isrs ? stamp : tbl;
         const DT sc = rank(d, v);
         if (valid && (tb <= tlim || d < lim) && sc < bd) {
@@ -1027,7 +1072,11 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         }
       }
     }
-    if (tabu && su == r && s >= sv && s < sv + slen) S.tabu[(s - sv) * NT + tid] = stamp;
+    if constexpr (kInterleave) {
+      if (tabu && irs >= 0) S.tabu[irs * NT + tid] = stamp;
+    } else {
+      if (tabu && su == r && s >= sv && s < sv + slen) S.tabu[(s - sv) * NT + tid] = stamp;
+    }
   };
 
   // Phase X of move (r, s): from the maintained products (kProductM), or
@@ -1050,7 +1099,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     for (int i = 0; i < MAXPT; ++i)
       if (i < slen && dl.get(i) < bd) {
         bd = dl.get(i);
-        bk = ukey | (uint32_t)(sv + i);
+        bk = ukey | (uint32_t)(sv + i * sk);
       }
     for (;;) {
       if (dmoves >= cap) break;
@@ -1114,7 +1163,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       const bool adm = S.tabu[i * NT + tid] <= 1 || (a.aspiration && cur + d < best);
       if (i < slen && adm && d < bd) {
         bd = d;
-        bk = ukey | (uint32_t)(sv + i);
+        bk = ukey | (uint32_t)(sv + i * sk);
       }
     }
   }
@@ -1164,7 +1213,8 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         Mn = t;
       }
       int stamp = it + tenure;
-      const bool owner = su == r && s >= sv && s < sv + slen;
+      const bool owner =
+          su == r && (kInterleave ? slot_of(s) >= 0 : s >= sv && s < sv + slen);
       if (period == 0 && (owner || (EXT && a.crit != 0))) {
         // the paper's rule: a fresh tenure per move, drawn by the owner only
         // (by every thread when the other criteria restamp touching pairs)
@@ -1189,7 +1239,11 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
                                : max(unit_mark(u), unit_mark(v));
           };
           if (su == r || su == s) {
-            for (int i = 0; i < slen; ++i) S.tabu[i * NT + tid] = mark(su, sv + i);
+            for (int i = 0; i < slen; ++i) S.tabu[i * NT + tid] = mark(su, sv + i * sk);
+          } else if constexpr (kInterleave) {
+            const int ir = slot_of(r), is = slot_of(s);
+            if (ir >= 0) S.tabu[ir * NT + tid] = mark(su, r);
+            if (is >= 0) S.tabu[is * NT + tid] = mark(su, s);
           } else {
             if (r >= sv && r < sv + slen) S.tabu[(r - sv) * NT + tid] = mark(su, r);
             if (s >= sv && s < sv + slen) S.tabu[(s - sv) * NT + tid] = mark(su, s);
@@ -1241,7 +1295,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* ws = a.ws ? a.ws + a.ws_stride * blockIdx.x : nullptr;
   const WalkSmem<DT, FE> S = smem_views<DT, FE, NT, MAXPT, STORE>(smem, a.inst, ws);
-  const Segment seg = make_segment<MAXPT>(a.inst.n);
+  const Segment seg = make_segment<MAXPT, interleaved<FE, NT>()>(a.inst.n);
   load_instance<DT, FE, NT, STORE>(S, a.inst);
   for (int w = blockIdx.x; w < a.walks; w += gridDim.x) {
     const int wi = a.walk_offset + w;
@@ -1272,7 +1326,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) batch_kernel(const BatchAr
     if (inst != cur_inst) {
       I = b.insts[inst];
       S = smem_views<DT, FE, NT, MAXPT, STORE>(smem, I, ws);
-      seg = make_segment<MAXPT>(I.n);
+      seg = make_segment<MAXPT, interleaved<FE, NT>()>(I.n);
       load_instance<DT, FE, NT, STORE>(S, I);
       cur_inst = inst;
     }
