@@ -98,8 +98,9 @@ qap_status occupancy(Launch* L, int sms, int work) {
 }
 
 qap_status plan_ctx(qap_ctx* ctx, const qap_search_params* p, Launch* L) {
-  if (!choose_plan_fit(ctx->di.n, p->threads_per_walk, &ctx->di, 1, ctx->fbytes, ctx->dbytes,
-                       ctx->smem_optin, 0, &L->plan))
+  const bool many = p->starts >= 2 * ctx->sms;
+  if (!choose_plan_fit(ctx->di.n, p->threads_per_walk, many, &ctx->di, 1, ctx->fbytes,
+                       ctx->dbytes, ctx->smem_optin, 0, &L->plan))
     return QAP_EUNSUPPORTED;
   L->fn = reinterpret_cast<const void*>(pick_walk_kernel(ctx->dbytes, ctx->fbytes, L->plan));
   if (!L->fn) return QAP_EUNSUPPORTED;
@@ -110,7 +111,8 @@ qap_status plan_ctx(qap_ctx* ctx, const qap_search_params* p, Launch* L) {
 
 qap_status plan_batch(qap_batch* b, const qap_search_params* p, Launch* L) {
   // the batch kernel also holds one static int
-  if (!choose_plan_fit(b->nmax, p->threads_per_walk, b->di.data(), b->count, b->fbytes,
+  const bool many = (int64_t)b->count * p->starts >= 2 * (int64_t)b->sms;
+  if (!choose_plan_fit(b->nmax, p->threads_per_walk, many, b->di.data(), b->count, b->fbytes,
                        b->dbytes, b->smem_optin, 16, &L->plan))
     return QAP_EUNSUPPORTED;
   L->fn = reinterpret_cast<const void*>(pick_batch_kernel(b->dbytes, b->fbytes, L->plan));
@@ -177,8 +179,10 @@ qap_status plan_classes(qap_batch* b, const qap_search_params* p) {
       continue;
     }
     // the batch kernel also holds one static int
-    if (!choose_plan_fit(b->di[i].n, p->threads_per_walk, &b->di[i], 1, b->fbytes, b->dbytes,
-                         b->smem_optin, 16, &plan_of[i]))
+    // the classes run together: walks of the whole batch fill the SMs
+    const bool many = (int64_t)b->count * W >= 2 * (int64_t)b->sms;
+    if (!choose_plan_fit(b->di[i].n, p->threads_per_walk, many, &b->di[i], 1, b->fbytes,
+                         b->dbytes, b->smem_optin, 16, &plan_of[i]))
       return QAP_EUNSUPPORTED;
   }
   std::vector<int> order(b->count);

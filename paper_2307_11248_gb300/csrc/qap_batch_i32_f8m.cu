@@ -11,6 +11,8 @@ namespace qapk {
     case 128124: return K<DT, FE, 128, 12, kProductM>;           \
     case 256064: return K<DT, FE, 256, 6, kProductM>;            \
     case 256084: return K<DT, FE, 256, 8, kProductM>;            \
+    case 256124: return K<DT, FE, 256, 12, kProductM>;           \
+    case 256164: return K<DT, FE, 256, 16, kProductM>;           \
     case 512044: return K<DT, FE, 512, 4, kProductM>;            \
     case 512084: return K<DT, FE, 512, 8, kProductM>;            \
     case 512124: return K<DT, FE, 512, 12, kProductM>;           \

@@ -66,8 +66,13 @@ inline constexpr Plan kLargePlan = {1024, 40, qapk::kGlobalDelta};
 // with at most eight slots, or 512 threads with any slot count (measured
 // 18-55 % faster than 1024 threads where both fit, n = 90..100), else the
 // fewest threads that fit at all; for a given thread count the fewest slots
-// that fit.
+// that fit.  With walks enough for two CTAs on every SM it also takes 256
+// threads with any slot count, when two of them fit an SM's shared memory:
+// two walks per SM then beat one at 512 threads (1216 walks: n = 80
+// asymmetric 9.1 vs 11.5 ms, n = 100 12.4 vs 14.6 ms, grid100 38.3 vs
+// 45.7 ms, int64 n = 100 16.2 vs 18.8 ms).
 inline constexpr Plan kPlans[] = {{128, 4, 0},   {128, 12, 0},  {256, 6, 0},   {256, 8, 0},
+                       {256, 12, 0},  {256, 16, 0},  {256, 24, 0},
                        {512, 4, 0},   {512, 8, 0},   {512, 12, 0},  {512, 16, 0},
                        {512, 20, 0},  {512, 24, 0},  {1024, 8, 0},  {1024, 12, 0},
                        {1024, 16, 0}, {1024, 20, 0}};
@@ -81,12 +86,13 @@ inline bool plan_for(int n, int nt, Plan* out) {
   return false;
 }
 
-inline bool choose_plan(int n, int threads, Plan* out) {
+inline bool choose_plan(int n, int threads, bool many, Plan* out) {
   if (threads != 0) return plan_for(n, threads, out);
   for (int pass = 0; pass < 2; ++pass)
     for (int nt : {128, 256, 512, 1024}) {
       Plan p;
-      if (plan_for(n, nt, &p) && (pass == 1 || p.maxpt <= 8 || nt == 512)) {
+      if (plan_for(n, nt, &p) &&
+          (pass == 1 || p.maxpt <= 8 || nt == 512 || (many && nt == 256))) {
         *out = p;
         return true;
       }
@@ -206,7 +212,7 @@ inline int plan_smem(const Plan& p, const DevInstance* d, int count, int fbytes,
 
 // Register plans compiled with the maintained products M (int8 flows).
 inline bool has_product_form(const Plan& p) {
-  return p.store == 0 && (p.nt == 1024 ? p.maxpt <= 12 : p.nt < 512 || p.maxpt <= 16);
+  return p.store == 0 && (p.nt == 1024 ? p.maxpt <= 12 : p.maxpt <= 16);
 }
 
 // The products form of a register plan when the flows are int8, an
@@ -227,13 +233,27 @@ inline Plan with_products(Plan p, const DevInstance* d, int count, int fbytes, i
 
 // A register plan when one holds n and fits shared memory (in its products
 // form when that fits as well); else the large-n plan, with F in global
-// memory when it does not fit shared memory either.
-inline bool choose_plan_fit(int nmax, int threads, const DevInstance* d, int count, int fbytes,
-                     int dbytes, int smem_optin, int reserve, Plan* out) {
+// memory when it does not fit shared memory either.  `many`: the launch has
+// walks enough for two CTAs on every SM (see choose_plan); a 256-thread plan
+// taken for that alone must let two CTAs share an SM (without the products
+// form if need be), else the choice is made as without `many`.
+inline bool choose_plan_fit(int nmax, int threads, bool many, const DevInstance* d, int count,
+                            int fbytes, int dbytes, int smem_optin, int reserve, Plan* out) {
   Plan p;
-  if (nmax <= 181 && choose_plan(nmax, threads, &p) &&
+  if (nmax <= 181 && choose_plan(nmax, threads, many, &p) &&
       plan_smem(p, d, count, fbytes, dbytes) + reserve <= smem_optin) {
-    *out = with_products(p, d, count, fbytes, dbytes, smem_optin, reserve);
+    Plan m = with_products(p, d, count, fbytes, dbytes, smem_optin, reserve);
+    if (many && threads == 0 && p.nt == 256 && p.maxpt > 8) {
+      // two CTAs per SM: each with its own 1 KB reserved by the hardware
+      auto two = [&](const Plan& x) {
+        return 2 * (plan_smem(x, d, count, fbytes, dbytes) + reserve + 1024) <= smem_optin + 1024;
+      };
+      if (!two(m)) m = p;
+      if (!two(m))
+        return choose_plan_fit(nmax, threads, false, d, count, fbytes, dbytes, smem_optin,
+                               reserve, out);
+    }
+    *out = m;
     return true;
   }
   if (threads != 0 && threads != kLargePlan.nt) return false;

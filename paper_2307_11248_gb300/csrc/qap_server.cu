@@ -134,7 +134,9 @@ namespace {
 // Plans the launch and sizes the device block of one request.
 qap_status place(qap_server* sv, Request* r) {
   const int W = r->params.starts, n = r->di.n;
-  if (!choose_plan_fit(n, r->params.threads_per_walk, &r->di, 1, r->fbytes, r->dbytes,
+  // a request's own walks decide (several requests share the GPU)
+  const bool many = W >= 2 * sv->sms;
+  if (!choose_plan_fit(n, r->params.threads_per_walk, many, &r->di, 1, r->fbytes, r->dbytes,
                        sv->smem_optin, 0, &r->plan))
     return QAP_EUNSUPPORTED;
   r->fn = reinterpret_cast<const void*>(pick_walk_kernel(r->dbytes, r->fbytes, r->plan));

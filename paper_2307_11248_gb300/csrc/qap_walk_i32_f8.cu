@@ -13,6 +13,9 @@ WalkKernelFn walk_kernel_i32_f8m(int nt, int maxpt, int store);  // qap_walk_i32
     case 128120: return K<DT, FE, 128, 12, 0>;                   \
     case 256060: return K<DT, FE, 256, 6, 0>;                    \
     case 256080: return K<DT, FE, 256, 8, 0>;                    \
+    case 256120: return K<DT, FE, 256, 12, 0>;                   \
+    case 256160: return K<DT, FE, 256, 16, 0>;                   \
+    case 256240: return K<DT, FE, 256, 24, 0>;                   \
     case 512040: return K<DT, FE, 512, 4, 0>;                    \
     case 512080: return K<DT, FE, 512, 8, 0>;                    \
     case 512120: return K<DT, FE, 512, 12, 0>;                   \
