@@ -153,8 +153,11 @@ typedef struct {
   int32_t aspiration;      /* 0 or 1                                         */
   uint64_t seed;           /* Philox key                                     */
   int32_t launch;          /* QAP_LAUNCH_PERSISTENT or QAP_LAUNCH_PLAIN      */
-  int32_t threads_per_walk;/* 0 = automatic; else 128, 256, 512 or 1024
-                              (n > 181 always uses 1024)                     */
+  int32_t threads_per_walk;/* 0 = automatic: the fewest threads holding n
+                              with at most 8 pairs per thread, or 512 with
+                              any; with starts >= 2 x SMs also 256 with any
+                              (two walks per SM).  Else 128, 256, 512 or
+                              1024 (n > 181 always uses 1024)                */
   int32_t tenure_per_n;    /* 1: tenure.tmin, tmax, period are hundredths of
                               each instance's n:
                               tmin' = max(1, floor(tmin n / 100)),
@@ -226,8 +229,8 @@ qap_status qap_search(qap_ctx* ctx, const qap_search_params* params, const int32
  *   out      device pointers, valid until the stream reaches the end of the
  *            call's work.
  *   stream   a cudaStream_t (NULL = legacy default stream).
- * Kernel launches only; capturable into a CUDA graph once the same
- * (n, threads_per_walk, delta width) has been run once outside capture.
+ * Kernel launches only; capturable into a CUDA graph once a search with the
+ * same n, starts, threads_per_walk and delta width has run outside capture.
  * Errors: QAP_EINVAL, QAP_EUNSUPPORTED, QAP_ECUDA (launch errors only). */
 qap_status qap_search_async(qap_ctx* ctx, const qap_search_params* params,
                             const int32_t* d_starts, const qap_walk_outputs* out,
@@ -300,7 +303,8 @@ qap_status qap_batch_info(const qap_batch* b, int32_t* count, int32_t* nmax,
                           int32_t* delta_bytes);
 
 /* Launch shape of a batch search.  Each instance takes the plan its own n
- * would get alone; instances with the same plan form a size class with one
+ * would get alone in a launch of the batch's total walks (or the plan the
+ * autotuner kept); instances with the same plan form a size class with one
  * persistent launch, and the classes run concurrently on internal streams
  * forked from and joined back into the caller's stream.  Reports the class
  * of the largest n and the number of classes. */
