@@ -250,10 +250,12 @@ def main():
     if args.workload != "asym50" and args.impl == "ours":
         return other_workloads(args)
 
-    world, rank, local = dist_setup()
     if args.impl == "reference":
-        run_reference(args, world, rank)
+        # rank 0 alone times the oracle on the host cores; no process group
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")),
+                      int(os.environ.get("RANK", "0")))
         return
+    world, rank, local = dist_setup()
 
     import torch
     import paper_2307_11248_gb300 as q
