@@ -733,6 +733,8 @@ qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
         fn<<<c.grid, c.plan.nt, c.smem, b->stream>>>(a);
         if (rep) cudaEventRecord(t1, b->stream);
       }
+      // a trial that did not launch would time as the fastest
+      if ((st = chk(cudaGetLastError(), "autotune launch")) != QAP_OK) return fail(st);
       if ((st = chk(cudaEventSynchronize(t1), "autotune trial")) != QAP_OK) return fail(st);
       cudaEventElapsedTime(&ms, t0, t1);
       const bool is_rule = cand.nt == rc.plan.nt && cand.maxpt == rc.plan.maxpt &&
