@@ -1,0 +1,128 @@
+"""GPU parity at the launch shapes that full-size launches take.
+
+A launch with walks enough for two CTAs on every SM (at least 2 x SMs walks)
+lets the automatic plan take 256 threads per walk with 8, 12, 16 or 24 pair
+slots per thread, two walks per SM.  Those plans are what the n = 100 grid
+workload (1024 walks x (2opt + 10^4 tabu iterations), Sections 4.1-4.4) and
+every many-walk launch of n = 54..100 run.  Here each of them is reached by
+the automatic choice itself, the plan is asserted, and sampled walks of the
+launch are compared with the CPU oracle bit for bit: best permutation, best
+and final cost, best iteration, iteration count, status, 2opt move count and
+both trajectory hashes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2307_11248_gb300 as q
+from paper_2307_11248_gb300 import instances
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ["best_p", "best_cost", "final_cost", "best_iter", "iters_done", "status",
+          "descent_moves", "hash", "descent_hash"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test selected but no CUDA device is available")
+    oracle.build()
+    q.lib()
+    return torch
+
+
+def sms():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def check_rows(g, F, D, rows, **kw):
+    o = oracle.run_walks(F, D, len(rows), walk_ids=np.asarray(rows), **kw)
+    for k in FIELDS:
+        a = g[k][rows].astype(np.int64)
+        b = o[k].astype(np.int64)
+        assert np.array_equal(a, b), (k, rows)
+
+
+def test_grid100_full_launch_on_its_own_plan():
+    """The whole n = 100 grid workload in the launch its benchmark times
+    (1024 walks, 2opt to a local minimum, then 10^4 tabu iterations): the
+    automatic plan is 256 threads x 24 slots, two CTAs per SM; sampled walks
+    equal the oracle's."""
+    w = instances.workload_grid100()
+    W = w["walks"]
+    assert W >= 2 * sms()
+    with q.Instance(w["F"], w["D"]) as inst:
+        prm = q.make_params(W, seed=w["seed"], iters=w["iters"], tenure=w["tenure"],
+                            descend=True)
+        plan = inst.plan(prm)
+        assert (plan["threads_per_walk"], plan["pairs_per_thread"]) == (256, 24), plan
+        assert plan["ctas_per_sm"] == 2 and plan["products"] == 0, plan
+        g = inst.search(prm)
+    assert (g["iters_done"] == w["iters"]).all()
+    check_rows(g, w["F"], w["D"], [0, 1, 511, 700, 1022, 1023], seed=w["seed"],
+               iters=w["iters"], tenure=w["tenure"], descend=True)
+    # every walk: its best permutation's Eq. 1 cost is its best cost
+    with q.Instance(w["F"], w["D"]) as inst:
+        assert np.array_equal(inst.cost(g["best_p"]), g["best_cost"])
+
+
+# (n, symmetric, expected slots, expected products form): every int8 plan with
+# 256 threads that a many-walk launch selects, symmetric instances (the
+# dot-product form of phase X) and asymmetric ones (the products form where
+# it is compiled, up to 16 slots; the dot-product form at 24)
+PLANS_256 = [(50, False, 6, 1), (52, True, 6, 0),
+             (58, False, 8, 1), (60, True, 8, 0),
+             (70, False, 12, 1), (66, True, 12, 0),
+             (80, False, 16, 1), (78, True, 16, 0),
+             (96, False, 24, 0), (90, True, 24, 0)]
+
+
+@pytest.mark.parametrize("n,sym,slots,products", PLANS_256)
+def test_many_walk_plans_int8(n, sym, slots, products):
+    W = 2 * sms()
+    F, D = instances.uniform_instance(n, 600 + n, symmetric=sym)
+    tn = instances.periodic_tenure(n)
+    iters = 400
+    with q.Instance(F, D) as inst:
+        assert inst.info["delta_bytes"] == 4
+        prm = q.make_params(W, seed=31, iters=iters, tenure=tn, descend=True)
+        plan = inst.plan(prm)
+        assert plan["threads_per_walk"] == 256 and plan["pairs_per_thread"] == slots, plan
+        assert plan["products"] == products and plan["ctas_per_sm"] >= 2, plan
+        g = inst.search(prm)
+    check_rows(g, F, D, [0, 5, W // 2 + 1, W - 1], seed=31, iters=iters, tenure=tn,
+               descend=True)
+
+
+@pytest.mark.parametrize("n,sym,slots", [(58, False, 8), (70, False, 12), (80, True, 16),
+                                         (96, False, 24)])
+def test_many_walk_plans_int16_flows(n, sym, slots):
+    """Flows beyond a byte take the int16 element path (interleaved slots)."""
+    W = 2 * sms()
+    F, D = instances.uniform_instance(n, 700 + n, symmetric=sym, hi=99)
+    F = F * 20  # up to 1980: int16 flows, still int32 deltas
+    tn = instances.periodic_tenure(n)
+    with q.Instance(F, D) as inst:
+        assert inst.info["delta_bytes"] == 4
+        prm = q.make_params(W, seed=32, iters=300, tenure=tn)
+        plan = inst.plan(prm)
+        assert plan["threads_per_walk"] == 256 and plan["pairs_per_thread"] == slots, plan
+        g = inst.search(prm)
+    check_rows(g, F, D, [1, W // 3, W - 2], seed=32, iters=300, tenure=tn)
+
+
+@pytest.mark.parametrize("n,slots", [(58, 8), (70, 12), (80, 16)])
+def test_fewer_walks_same_plan_by_request(n, slots):
+    """The same 256-thread plans asked for explicitly with a few walks (one
+    per SM at most): the launch shape does not change the walks."""
+    F, D = instances.uniform_instance(n, 800 + n, symmetric=False)
+    tn = instances.periodic_tenure(n)
+    with q.Instance(F, D) as inst:
+        prm = q.make_params(5, seed=33, iters=500, tenure=tn, threads_per_walk=256)
+        plan = inst.plan(prm)
+        assert plan["pairs_per_thread"] == slots, plan
+        g = inst.search(prm)
+    check_rows(g, F, D, list(range(5)), seed=33, iters=500, tenure=tn)
