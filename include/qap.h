@@ -37,9 +37,19 @@
  *   - The per-walk trajectory hash is FNV-1a/64 over the applied moves:
  *     h = 14695981039346656037; per move h ^= (r << 16 | s); h *= 1099511628211.
  *
- * Arithmetic is exact integer arithmetic.  The library keeps deltas in int32
- * when the bound B = (n^2 + 8n + 32) * max|F| * max|D| is at most
- * 2^31 - 2, and in int64 otherwise (or when QAP_FORCE_INT64 is given).
+ * Arithmetic is exact integer arithmetic for any int64 F and D whose bound
+ * B = (n^2 + 8n + 32) * max|F| * max|D| is below 2^62 (else QAP_EOVERFLOW).
+ * Deltas are int32 when B is at most 2^31 - 2 and the instance is on a
+ * narrow element path, else int64 (also when QAP_FORCE_INT64 is given).
+ * Element paths, chosen per instance (per batch: the widest any instance
+ * needs):
+ *   int8 F, int8 D    every difference of two F entries and of two D
+ *                     entries fits a byte, and the deltas are int32;
+ *   int16 F, int8 D   F fits int16, D fits int8, and 2 n max|F| max|D| is
+ *                     below 2^31 (the dot products of phase X sum in 32 bits);
+ *   int64 F, int64 D  every other instance: int64 storage and arithmetic, F
+ *                     read from global memory, P in shared memory while it
+ *                     fits and in a per-CTA device workspace otherwise.
  *
  * Errors: every entry point returns a qap_status; on error nothing has been
  * written to the outputs unless stated otherwise.  A CUDA error is returned
@@ -61,12 +71,14 @@ typedef struct qap_ctx qap_ctx;  /* opaque: device copies of F and D */
 typedef enum {
   QAP_OK = 0,
   QAP_EINVAL = 1,        /* invalid argument (n < 2, bad permutation, ...)      */
-  QAP_EOVERFLOW = 2,     /* the bound B does not fit the int64 path (>= 2^62)   */
+  QAP_EOVERFLOW = 2,     /* the bound B does not fit the int64 path (>= 2^62),
+                            or a frequency penalty does not fit the deltas      */
   QAP_ENOMEM = 3,        /* device or host allocation failed                   */
   QAP_ECUDA = 4,         /* a CUDA runtime call failed; see qap_last_error()   */
   QAP_ETIMEOUT = 5,      /* a bounded wait ran out (serving loop)              */
-  QAP_EUNSUPPORTED = 6   /* instance outside the kernels' ranges: n > 256,
-                            F outside int16 or D outside int8                   */
+  QAP_EUNSUPPORTED = 6   /* outside what the kernels hold: n > 256, a thread
+                            count too small for n, or a form the entry point
+                            does not offer (see qap_last_error())             */
 } qap_status;
 
 /* Tabu tenure rule: t drawn uniformly from [tmin, tmax]; a new t every
@@ -106,11 +118,15 @@ typedef struct {
   int32_t sym_flow;        /* F == F^T                                      */
   int32_t sym_dist;        /* D == D^T                                      */
   int64_t bound;           /* B above                                       */
+  int32_t flow_bytes;      /* bytes per stored F element on the device: 1,
+                              2, or 8 on the int64 element path            */
+  int32_t dist_bytes;      /* bytes per stored D and P element: 1 or 8      */
 } qap_ctx_info;
 
 /* Create a context for one instance.
- *   F, D   host pointers to n*n int64 values, row-major.  Copied; the caller
- *          may free them when the call returns.  F must fit int16 and D int8.
+ *   F, D   host pointers to n*n int64 values, row-major, any sign.  Copied;
+ *          the caller may free them when the call returns.  The element path
+ *          and the delta width follow from the values (see above).
  *   n      2 <= n <= 256.  Up to n = 181 a walk keeps its deltas in
  *          registers; beyond, in a workspace in device memory (allocated by
  *          the library on first use), with F in shared or global memory.
@@ -343,6 +359,44 @@ qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
                               int32_t trial_iters, qap_tune_result* results,
                               int32_t max_results, int32_t* nresults);
 
+/* One size class of a batch search: the instances that share a launch plan
+ * and the persistent launch that runs their walks. */
+typedef struct {
+  int32_t nmin, nmax;        /* n range of the class's instances             */
+  int32_t instances;
+  int32_t walks;             /* walks of the launch (instances x starts)     */
+  int32_t threads_per_walk;
+  int32_t pairs_per_thread;
+  int32_t products;          /* 1: phase X from maintained products          */
+  int32_t workspace;         /* 1: deltas and marks in the device workspace  */
+  int32_t grid;              /* CTAs of the launch                           */
+  int32_t ctas_per_sm;
+  int32_t smem_bytes;        /* dynamic shared memory per CTA                */
+  int32_t delta_bytes;       /* 4 or 8, as for the whole batch               */
+  int32_t flow_bytes;        /* bytes per stored F element                   */
+  int32_t dist_bytes;        /* bytes per stored D and P element             */
+  float last_ms;             /* device time of the class's kernel in the
+                                last search made with timing on (CUDA events
+                                on the stream the kernel ran on), else -1   */
+} qap_class_info;
+
+/* Timing of the classes' kernels: with on = 1, each later search of the
+ * batch records a CUDA event before and after each class's kernel launch, on
+ * the stream the launch uses; qap_batch_classes reports the elapsed time.
+ * Off (0) by default; a search with timing on should not be captured in a
+ * CUDA graph.  Errors: QAP_EINVAL. */
+qap_status qap_batch_set_timing(qap_batch* b, int32_t on);
+
+/* The size classes a search like `params` runs (plans them if needed, as
+ * qap_batch_plan does): up to max_out entries into out (may be NULL when
+ * 0), the number of classes into *count (may be NULL), and the class index
+ * of every instance into inst_class[count of the batch] (may be NULL).
+ * last_ms waits for the last timed launch of the class to finish.
+ * Errors: QAP_EINVAL, QAP_EUNSUPPORTED, QAP_ECUDA. */
+qap_status qap_batch_classes(qap_batch* b, const qap_search_params* params,
+                             qap_class_info* out, int32_t max_out, int32_t* count,
+                             int32_t* inst_class);
+
 /* Run params->starts walks of every instance.  Output row i * starts + k
  * holds walk k of instance i; best_p rows hold p_stride >= max n elements
  * (the first n[i] are the permutation).  params->launch must be
@@ -383,11 +437,16 @@ typedef struct {
   double queued_us;   /* submit -> admission                                */
   double device_us;   /* admission -> results on the host                   */
   double total_us;    /* submit -> results on the host                      */
+  double kernel_start_us;  /* the request's search kernel on the device clock
+                              (CUDA events on its stream), microseconds from
+                              the server's creation; -1 if not measured     */
+  double kernel_end_us;
 } qap_request_times;
 
 typedef struct {
   int64_t submitted, completed, pending, in_flight;
   int64_t arena_bytes, arena_used;
+  int64_t peak_in_flight;  /* most requests admitted at once so far        */
 } qap_server_stats;
 
 /* Start a server on the current device.  Errors: QAP_EINVAL, QAP_ENOMEM,
@@ -427,8 +486,11 @@ void qap_server_destroy(qap_server* s);
  * outputs, stream-ordered kernel launch), but the work-queue counter, the
  * instance table and the item lists live in one static device array of
  * about 1 MiB compiled into the library, held by every GPU that loads the
- * library until the process exits.  The call performs no cudaMalloc,
- * cudaFree or other allocating routine, on the device or on the host.
+ * library until the process exits.  The call performs no cudaMalloc or
+ * cudaFree and no other device allocation, and its host-side bookkeeping
+ * uses fixed-size static tables (no heap allocation either).  It makes the
+ * batch's device current for its own work and gives the caller's current
+ * device back on return.
  *
  * Limits: at most 4096 instances and at most 65536 walks in total
  * (count x params->starts); larger calls return QAP_EINVAL and
@@ -440,7 +502,10 @@ void qap_server_destroy(qap_server* s);
  * rewrites the tables and zeroes the counter before its kernel starts, so
  * two calls whose kernels overlap on the GPU race on the array; order them
  * on one stream or synchronise between them.  The call copies its tables
- * from static host memory, so it may wait until the stream reaches them. */
+ * from static host memory, so it may wait until the stream reaches them.
+ * For the same reason it returns QAP_EUNSUPPORTED, and launches nothing,
+ * while `stream` is being captured: a captured copy would read host tables
+ * that later calls overwrite. */
 qap_status qap_batch_search_noalloc(qap_batch* b, const qap_search_params* params,
                                     const qap_walk_outputs* out, int32_t p_stride, void* stream);
 

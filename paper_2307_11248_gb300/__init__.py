@@ -11,7 +11,7 @@ from ._binding import (  # noqa: F401
     qap_2opt, qap_cost, qap_create, qap_destroy, qap_info, qap_plan, qap_search,
     qap_search_async, qap_tabu, strerror, last_error, Batch, qap_batch_create, qap_batch_destroy,
     qap_batch_info, qap_batch_plan, qap_batch_search, qap_batch_search_async, qap_batch_autotune,
-    qap_best_walks,
+    qap_best_walks, qap_batch_set_timing, qap_batch_classes,
     qap_batch_search_noalloc, Server, qap_server_create, qap_server_destroy,
     qap_server_get_stats, qap_server_submit, qap_server_wait, TABU_PAIR, TABU_UNIT_LOC, TABU_UNIT,
 )

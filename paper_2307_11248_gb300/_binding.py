@@ -39,7 +39,8 @@ class Tenure(ctypes.Structure):
 class CtxInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("delta_bytes", ctypes.c_int32),
                 ("sym_flow", ctypes.c_int32), ("sym_dist", ctypes.c_int32),
-                ("bound", ctypes.c_int64)]
+                ("bound", ctypes.c_int64), ("flow_bytes", ctypes.c_int32),
+                ("dist_bytes", ctypes.c_int32)]
 
 
 class SearchParams(ctypes.Structure):
@@ -64,12 +65,14 @@ class ServerConfig(ctypes.Structure):
 
 class RequestTimes(ctypes.Structure):
     _fields_ = [("queued_us", ctypes.c_double), ("device_us", ctypes.c_double),
-                ("total_us", ctypes.c_double)]
+                ("total_us", ctypes.c_double), ("kernel_start_us", ctypes.c_double),
+                ("kernel_end_us", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in
-                ("submitted", "completed", "pending", "in_flight", "arena_bytes", "arena_used")]
+                ("submitted", "completed", "pending", "in_flight", "arena_bytes", "arena_used",
+                 "peak_in_flight")]
 
 
 class PlanInfo(ctypes.Structure):
@@ -84,6 +87,14 @@ class TuneResult(ctypes.Structure):
                 ("pairs_per_thread", ctypes.c_int32), ("workspace", ctypes.c_int32),
                 ("products", ctypes.c_int32), ("trial_ms", ctypes.c_float),
                 ("rule_ms", ctypes.c_float)]
+
+
+class ClassInfo(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int32) for name in
+                ("nmin", "nmax", "instances", "walks", "threads_per_walk", "pairs_per_thread",
+                 "products", "workspace", "grid", "ctas_per_sm", "smem_bytes", "delta_bytes",
+                 "flow_bytes", "dist_bytes")] + \
+               [("last_ms", ctypes.c_float)]
 
 
 OUTPUT_FIELDS = {  # name -> (dtype, per-walk shape multiplier uses n)
@@ -142,6 +153,12 @@ def lib():
                                              ctypes.POINTER(TuneResult), i32,
                                              ctypes.POINTER(i32)]
             L.qap_batch_autotune.restype = st
+            L.qap_batch_set_timing.argtypes = [vp, i32]
+            L.qap_batch_set_timing.restype = st
+            L.qap_batch_classes.argtypes = [vp, ctypes.POINTER(SearchParams),
+                                            ctypes.POINTER(ClassInfo), i32, ctypes.POINTER(i32),
+                                            vp]
+            L.qap_batch_classes.restype = st
             L.qap_batch_search.argtypes = [vp, ctypes.POINTER(SearchParams),
                                            ctypes.POINTER(WalkOutputs), i32]
             L.qap_batch_search.restype = st
@@ -429,6 +446,24 @@ def qap_batch_search_async(h, params, d_out, p_stride, stream):
            "qap_batch_search_async")
 
 
+def qap_batch_set_timing(h, on):
+    _check(lib().qap_batch_set_timing(h, 1 if on else 0), "qap_batch_set_timing")
+
+
+def qap_batch_classes(h, params, count):
+    """The size classes of a batch search: a list of dicts (last_ms is the
+    last timed launch's device time, or -1) and the class of each instance."""
+    nc = ctypes.c_int32()
+    _check(lib().qap_batch_classes(h, ctypes.byref(params), None, 0, ctypes.byref(nc), None),
+           "qap_batch_classes")
+    arr = (ClassInfo * max(1, nc.value))()
+    of = np.zeros(count, dtype=np.int32)
+    _check(lib().qap_batch_classes(h, ctypes.byref(params), arr, nc.value, ctypes.byref(nc),
+                                   _ptr(of)), "qap_batch_classes")
+    return ([{k: getattr(arr[i], k) for k, _ in ClassInfo._fields_} for i in range(nc.value)],
+            of)
+
+
 def qap_batch_search_noalloc(h, params, d_out, p_stride, stream):
     """qap_batch_search_async without any allocation inside the call (its
     work queue and tables live in a static device array); see qap.h."""
@@ -472,6 +507,12 @@ class Batch:
 
     def search(self, params, freq=False):
         return qap_batch_search(self.h, params, self.p_stride, freq=freq)
+
+    def set_timing(self, on):
+        qap_batch_set_timing(self.h, on)
+
+    def classes(self, params):
+        return qap_batch_classes(self.h, params, self.info["count"])
 
     def device_outputs(self, walks, device="cuda"):
         import torch

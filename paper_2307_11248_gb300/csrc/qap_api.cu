@@ -20,6 +20,8 @@
 namespace qaph {
 thread_local char g_last_error[256] = "";
 std::mutex g_attr_mu;
+PreparedKernel g_prepared[kPreparedMax];
+int g_prepared_count = 0;
 }  // namespace qaph
 
 using namespace qaph;
@@ -31,7 +33,7 @@ struct qap_ctx {
   int fbytes = 2;  // flow element width in device memory (1: int8, 2: int16)
   void* dF = nullptr;
   void* dFt = nullptr;
-  int8_t* dD = nullptr;
+  void* dD = nullptr;
   cudaStream_t stream = nullptr;
   // growable device buffer of the blocking entry points
   void* scratch = nullptr;
@@ -49,8 +51,11 @@ struct BatchClass {
   std::vector<int> members;  // instance indices, largest n first
   int item_off = 0, items = 0;
   size_t ws_off = 0, ws_stride = 0;
+  size_t p_off = 0, rws_off = 0;  // offsets inside a CTA's workspace slice
   cudaStream_t side = nullptr;
   cudaEvent_t done = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;  // timing events (qap_batch_set_timing)
+  bool timed = false;                      // t0, t1 bracket the class's last launch
 };
 
 struct qap_batch {
@@ -74,6 +79,7 @@ struct qap_batch {
   int32_t* d_class_items = nullptr;  // per class item_inst | item_walk, then row_base
   cudaEvent_t fork = nullptr;
   std::vector<Plan> tuned;  // per instance: the autotuner's plan (nt == 0: none)
+  int timing = 0;           // record timing events around each class's launch
 };
 
 namespace {
@@ -124,6 +130,18 @@ qap_status plan_batch(qap_batch* b, const qap_search_params* p, Launch* L) {
 
 int nt_index(int nt) { return nt == 128 ? 0 : nt == 256 ? 1 : nt == 512 ? 2 : 3; }
 
+void destroy_class_handles(BatchClass& c) {
+  if (c.side) {
+    cudaStreamSynchronize(c.side);
+    cudaStreamDestroy(c.side);
+  }
+  if (c.done) cudaEventDestroy(c.done);
+  if (c.t0) cudaEventDestroy(c.t0);
+  if (c.t1) cudaEventDestroy(c.t1);
+  c.side = nullptr;
+  c.done = c.t0 = c.t1 = nullptr;
+}
+
 // Launch shape of a class with W walks per member (smem, kernel, grid,
 // workspace) and the instance table for its thread count.
 qap_status class_shape(qap_batch* b, BatchClass& c, int W, const qap_search_params* p) {
@@ -143,14 +161,17 @@ qap_status class_shape(qap_batch* b, BatchClass& c, int W, const qap_search_para
   c.items = (int)c.members.size() * W;
   c.ctas_per_sm = occ;
   c.grid = std::min(c.items, occ * b->sms);
-  c.ws_stride = workspace_per_cta(c.plan, b->dbytes, nmax, p);
+  const WsLayout wl = ws_layout(c.plan, b->dbytes, b->fbytes, nmax, p);
+  c.ws_stride = wl.stride;
+  c.p_off = wl.p_off;
+  c.rws_off = wl.rws_off;
   const int t = nt_index(c.plan.nt);
   if (!(b->insts_written & (1 << t))) {
     std::vector<qapk::InstArgs> h(b->count);
     char* base = static_cast<char*>(b->data);
     for (int i = 0; i < b->count; ++i)
       h[i] = inst_args(b->di[i], base + b->offF[i], base + b->offFt[i],
-                       reinterpret_cast<int8_t*>(base + b->offD[i]), c.plan.nt, b->fbytes);
+                       base + b->offD[i], c.plan.nt, b->fbytes);
     QAP_CUDA(cudaMemcpy(b->d_insts + (size_t)t * b->count, h.data(),
                         sizeof(qapk::InstArgs) * b->count, cudaMemcpyHostToDevice));
     b->insts_written |= 1 << t;
@@ -210,17 +231,14 @@ qap_status plan_classes(qap_batch* b, const qap_search_params* p) {
     if (k < old.size()) {
       b->classes[k].side = old[k].side;
       b->classes[k].done = old[k].done;
+      b->classes[k].t0 = old[k].t0;
+      b->classes[k].t1 = old[k].t1;
       old[k].side = nullptr;
       old[k].done = nullptr;
+      old[k].t0 = old[k].t1 = nullptr;
     }
   }
-  for (BatchClass& c : old) {
-    if (c.side) {
-      cudaStreamSynchronize(c.side);
-      cudaStreamDestroy(c.side);
-    }
-    if (c.done) cudaEventDestroy(c.done);
-  }
+  for (BatchClass& c : old) destroy_class_handles(c);
   int item_off = 0;
   size_t ws_off = 0;
   for (BatchClass& c : b->classes) {
@@ -233,6 +251,7 @@ qap_status plan_classes(qap_batch* b, const qap_search_params* p) {
       if (!c.side) QAP_CUDA(cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking));
       if (!c.done) QAP_CUDA(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
     }
+    c.timed = false;
   }
   if (b->classes.size() > 1 && !b->fork)
     QAP_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
@@ -297,10 +316,10 @@ qap_status qap_create(const int64_t* F, const int64_t* D, int32_t n, uint32_t fl
     qap_destroy(c);
     return s;
   };
-  c->dbytes = ((flags & QAP_FORCE_INT64) || di.bound > (int64_t)INT_MAX - 1) ? 8 : 4;
+  c->dbytes = ((flags & QAP_FORCE_INT64) || di.wide || di.bound > (int64_t)INT_MAX - 1) ? 8 : 4;
   c->fbytes = flow_bytes(di, c->dbytes);
   di.ldF = pad_ldF(n, c->fbytes);
-  di.ldP = pad_ldP(n);
+  di.ldP = pad_ldP(n, pbytes_of(c->fbytes));
   c->di = di;
   qap_status st = device_attrs(&c->device, &c->sms, &c->smem_optin);
   if (st != QAP_OK) return fail(st);
@@ -339,13 +358,16 @@ qap_status qap_info(const qap_ctx* ctx, qap_ctx_info* out) {
   out->sym_flow = ctx->di.symF;
   out->sym_dist = ctx->di.symD;
   out->bound = ctx->di.bound;
+  out->flow_bytes = ctx->fbytes;
+  out->dist_bytes = pbytes_of(ctx->fbytes);
   return QAP_OK;
 }
 
 qap_status qap_plan(qap_ctx* ctx, const qap_search_params* params, qap_plan_info* out) {
   if (!ctx || !out) return QAP_EINVAL;
   QAP_TRY(validate_params(params));
-  QAP_CUDA(cudaSetDevice(ctx->device));
+  DeviceGuard dg;
+  QAP_TRY(dg.set(ctx->device));
   Launch L;
   QAP_TRY(plan_ctx(ctx, params, &L));
   out->threads_per_walk = L.plan.nt;
@@ -367,7 +389,8 @@ qap_status qap_search_async(qap_ctx* ctx, const qap_search_params* params,
   QAP_TRY(validate_params(params));
   if (!out || !out->best_cost) return QAP_EINVAL;
   QAP_TRY(check_penalty(params, ctx->dbytes, ctx->di.bound));
-  QAP_CUDA(cudaSetDevice(ctx->device));
+  DeviceGuard dg;
+  QAP_TRY(dg.set(ctx->device));
   Launch L;
   QAP_TRY(plan_ctx(ctx, params, &L));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -377,8 +400,10 @@ qap_status qap_search_async(qap_ctx* ctx, const qap_search_params* params,
   a.starts = d_starts;
   a.walks = params->starts;
   a.walk_offset = 0;
-  a.ws_stride = workspace_per_cta(L.plan, ctx->dbytes, ctx->di.n, params);
-  a.s.rws_off = delta_workspace(L.plan, ctx->dbytes);
+  const WsLayout wl = ws_layout(L.plan, ctx->dbytes, ctx->fbytes, ctx->di.n, params);
+  a.ws_stride = wl.stride;
+  a.s.rws_off = wl.rws_off;
+  a.s.p_off = wl.p_off;
   if (a.ws_stride) {
     // the plain form runs one CTA per launch; launches on one stream share it
     const int ctas = params->launch == QAP_LAUNCH_PLAIN ? 1 : L.grid;
@@ -410,7 +435,8 @@ qap_status qap_search(qap_ctx* ctx, const qap_search_params* params, const int32
     for (int w = 0; w < W; ++w)
       if (!is_permutation(starts + (size_t)w * n, n, seen)) return QAP_EINVAL;
   }
-  QAP_CUDA(cudaSetDevice(ctx->device));
+  DeviceGuard dg;
+  QAP_TRY(dg.set(ctx->device));
   const OutLayout L = out_layout(W, n);
   const size_t starts_off = (L.total + 255) / 256 * 256;
   const size_t freq_off = starts_off + ((size_t)W * n * 4 + 255) / 256 * 256;
@@ -434,7 +460,8 @@ qap_status qap_cost(qap_ctx* ctx, int32_t count, const int32_t* p, int64_t* cost
   std::vector<char> seen;
   for (int k = 0; k < count; ++k)
     if (!is_permutation(p + (size_t)k * n, n, seen)) return QAP_EINVAL;
-  QAP_CUDA(cudaSetDevice(ctx->device));
+  DeviceGuard dg;
+  QAP_TRY(dg.set(ctx->device));
   const size_t pbytes = (size_t)count * n * sizeof(int32_t);
   const size_t off_cost = ((pbytes + 255) / 256) * 256;
   QAP_TRY(grow(&ctx->scratch, &ctx->scratch_bytes, off_cost + (size_t)count * 8));
@@ -445,11 +472,17 @@ qap_status qap_cost(qap_ctx* ctx, int32_t count, const int32_t* p, int64_t* cost
   QAP_CUDA(cudaMemcpyAsync(dp, p, pbytes, cudaMemcpyHostToDevice, s));
   const int grid = std::min(count, ctx->sms * 8);
   if (ctx->fbytes == 1)
-    qapk::cost_kernel<int8_t, 256><<<grid, 256, 0, s>>>(static_cast<const int8_t*>(ctx->dF),
-                                                        ctx->di.ldF, ctx->dD, n, dp, count, dc);
+    qapk::cost_kernel<int8_t, int8_t, 256><<<grid, 256, 0, s>>>(
+        static_cast<const int8_t*>(ctx->dF), ctx->di.ldF, static_cast<const int8_t*>(ctx->dD), n,
+        dp, count, dc);
+  else if (ctx->fbytes == 2)
+    qapk::cost_kernel<int16_t, int8_t, 256><<<grid, 256, 0, s>>>(
+        static_cast<const int16_t*>(ctx->dF), ctx->di.ldF, static_cast<const int8_t*>(ctx->dD),
+        n, dp, count, dc);
   else
-    qapk::cost_kernel<int16_t, 256><<<grid, 256, 0, s>>>(static_cast<const int16_t*>(ctx->dF),
-                                                         ctx->di.ldF, ctx->dD, n, dp, count, dc);
+    qapk::cost_kernel<int64_t, int64_t, 256><<<grid, 256, 0, s>>>(
+        static_cast<const int64_t*>(ctx->dF), ctx->di.ldF, static_cast<const int64_t*>(ctx->dD),
+        n, dp, count, dc);
   QAP_CUDA(cudaGetLastError());
   QAP_CUDA(cudaMemcpyAsync(cost, dc, (size_t)count * 8, cudaMemcpyDeviceToHost, s));
   QAP_CUDA(cudaStreamSynchronize(s));
@@ -523,18 +556,20 @@ qap_status qap_batch_create(int32_t count, const int64_t* const* F, const int64_
   b->count = count;
   b->di.resize(count);
   int64_t maxB = 0;
-  int bytevec = 1;
+  int bytevec = 1, wide = 0;
   for (int i = 0; i < count; ++i) {
     qap_status st = inspect_instance(F[i], D[i], n[i], &b->di[i]);
     if (st != QAP_OK) return fail(st);
     bytevec &= b->di[i].bytevec;
+    wide |= b->di[i].wide;
     maxB = std::max(maxB, b->di[i].bound);
     b->nmax = std::max(b->nmax, n[i]);
   }
-  // one delta width and one flow width for the whole batch
-  b->dbytes = ((flags & QAP_FORCE_INT64) || maxB > (int64_t)INT_MAX - 1) ? 8 : 4;
+  // one delta width and one element width for the whole batch
+  b->dbytes = ((flags & QAP_FORCE_INT64) || wide || maxB > (int64_t)INT_MAX - 1) ? 8 : 4;
   DevInstance all;
   all.bytevec = bytevec;
+  all.wide = wide;
   b->fbytes = flow_bytes(all, b->dbytes);
   qap_status st = device_attrs(&b->device, &b->sms, &b->smem_optin);
   if (st != QAP_OK) return fail(st);
@@ -545,7 +580,7 @@ qap_status qap_batch_create(int32_t count, const int64_t* const* F, const int64_
   for (int i = 0; i < count; ++i) {
     DevInstance& d = b->di[i];
     d.ldF = pad_ldF(d.n, b->fbytes);
-    d.ldP = pad_ldP(d.n);
+    d.ldP = pad_ldP(d.n, pbytes_of(b->fbytes));
     std::vector<unsigned char> iF, iFt, iD;
     build_images(F[i], D[i], d, b->fbytes, iF, iFt, iD);
     auto append = [&](const std::vector<unsigned char>& v) {
@@ -579,13 +614,7 @@ void qap_batch_destroy(qap_batch* b) {
   if (b->scratch) cudaFree(b->scratch);
   if (b->ws) cudaFree(b->ws);
   if (b->d_class_items) cudaFree(b->d_class_items);
-  for (BatchClass& c : b->classes) {
-    if (c.side) {
-      cudaStreamSynchronize(c.side);
-      cudaStreamDestroy(c.side);
-    }
-    if (c.done) cudaEventDestroy(c.done);
-  }
+  for (BatchClass& c : b->classes) destroy_class_handles(c);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -603,7 +632,8 @@ qap_status qap_batch_info(const qap_batch* b, int32_t* count, int32_t* nmax,
 qap_status qap_batch_plan(qap_batch* b, const qap_search_params* params, qap_plan_info* out) {
   if (!b || !out) return QAP_EINVAL;
   QAP_TRY(validate_params(params));
-  QAP_CUDA(cudaSetDevice(b->device));
+  DeviceGuard dg;
+  QAP_TRY(dg.set(b->device));
   QAP_TRY(plan_classes(b, params));
   const BatchClass& c = b->classes.front();  // the class of the largest n
   out->threads_per_walk = c.plan.nt;
@@ -615,6 +645,54 @@ qap_status qap_batch_plan(qap_batch* b, const qap_search_params* params, qap_pla
   out->classes = (int32_t)b->classes.size();
   out->products = (c.plan.store & qapk::kProductM) != 0;
   out->workspace = (c.plan.store & qapk::kGlobalDelta) != 0;
+  return QAP_OK;
+}
+
+qap_status qap_batch_set_timing(qap_batch* b, int32_t on) {
+  if (!b || (on != 0 && on != 1)) return QAP_EINVAL;
+  b->timing = on;
+  return QAP_OK;
+}
+
+qap_status qap_batch_classes(qap_batch* b, const qap_search_params* params,
+                             qap_class_info* out, int32_t max_out, int32_t* count,
+                             int32_t* inst_class) {
+  if (!b || max_out < 0 || (max_out > 0 && !out)) return QAP_EINVAL;
+  QAP_TRY(validate_params(params));
+  DeviceGuard dg;
+  QAP_TRY(dg.set(b->device));
+  QAP_TRY(plan_classes(b, params));
+  if (count) *count = (int32_t)b->classes.size();
+  for (size_t k = 0; k < b->classes.size(); ++k) {
+    BatchClass& c = b->classes[k];
+    if (inst_class)
+      for (int i : c.members) inst_class[i] = (int32_t)k;
+    if ((int32_t)k >= max_out) continue;
+    qap_class_info& o = out[k];
+    o.nmin = INT_MAX;
+    o.nmax = 0;
+    for (int i : c.members) {
+      o.nmin = std::min(o.nmin, b->di[i].n);
+      o.nmax = std::max(o.nmax, b->di[i].n);
+    }
+    o.instances = (int32_t)c.members.size();
+    o.walks = c.items;
+    o.threads_per_walk = c.plan.nt;
+    o.pairs_per_thread = c.plan.maxpt;
+    o.products = (c.plan.store & qapk::kProductM) != 0;
+    o.workspace = (c.plan.store & qapk::kGlobalDelta) != 0;
+    o.grid = c.grid;
+    o.ctas_per_sm = c.ctas_per_sm;
+    o.smem_bytes = c.smem;
+    o.delta_bytes = b->dbytes;
+    o.flow_bytes = b->fbytes;
+    o.dist_bytes = pbytes_of(b->fbytes);
+    o.last_ms = -1.f;
+    if (c.timed) {
+      QAP_CUDA(cudaEventSynchronize(c.t1));
+      QAP_CUDA(cudaEventElapsedTime(&o.last_ms, c.t0, c.t1));
+    }
+  }
   return QAP_OK;
 }
 
@@ -635,7 +713,8 @@ qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
   tp.iters = trial_iters;
   QAP_TRY(validate_params(&tp));
   for (const DevInstance& d : b->di) QAP_TRY(check_penalty(&tp, b->dbytes, d.bound));
-  QAP_CUDA(cudaSetDevice(b->device));
+  DeviceGuard dg;
+  QAP_TRY(dg.set(b->device));
   b->tuned.clear();
   b->classes_threads = -1;
   QAP_TRY(plan_classes(b, &tp));
@@ -680,7 +759,9 @@ qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
     std::vector<Plan> cands;
     for (int nt : {128, 256, 512, 1024}) {
       Plan p;
-      if (nmax <= 181 && plan_for(nmax, nt, &p) && fits(p)) {
+      if (nmax <= 181 && plan_for(nmax, nt, &p) &&
+          fits(p = wide_store(p, dm.data(), (int)dm.size(), b->fbytes, b->dbytes,
+                              b->smem_optin, 16))) {
         cands.push_back(p);
         Plan m = p;
         m.store |= qapk::kProductM;
@@ -690,7 +771,10 @@ qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
     }
     if (qapk::row_segments(nmax, kLargePlan.maxpt) <= kLargePlan.nt) {
       Plan p = kLargePlan;
-      if (!fits(p)) p.store |= qapk::kGlobalFlow;
+      if (b->fbytes == 8)
+        p = wide_store(p, dm.data(), (int)dm.size(), b->fbytes, b->dbytes, b->smem_optin, 16);
+      else if (!fits(p))
+        p.store |= qapk::kGlobalFlow;
       if (fits(p)) cands.push_back(p);
     }
     // items of this class, longest instances first; row bases for all
@@ -722,7 +806,8 @@ qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
       a.items = c.items;
       a.counter = counter;
       a.s = make_search_args(&tp, &dout, b->nmax);
-      a.s.rws_off = delta_workspace(c.plan, b->dbytes);
+      a.s.rws_off = c.rws_off;
+      a.s.p_off = c.p_off;
       a.ws_stride = c.ws_stride;
       a.ws = c.ws_stride ? static_cast<unsigned char*>(b->ws) : nullptr;
       const auto fn = reinterpret_cast<qapk::BatchKernelFn>(const_cast<void*>(c.fn));
@@ -774,15 +859,18 @@ qap_status qap_batch_search_async(qap_batch* b, const qap_search_params* params,
   if (!out || !out->best_cost || p_stride < b->nmax) return QAP_EINVAL;
   if (params->launch != QAP_LAUNCH_PERSISTENT) return QAP_EINVAL;
   for (const DevInstance& d : b->di) QAP_TRY(check_penalty(params, b->dbytes, d.bound));
-  QAP_CUDA(cudaSetDevice(b->device));
+  DeviceGuard dg;
+  QAP_TRY(dg.set(b->device));
   QAP_TRY(plan_classes(b, params));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t total = (size_t)b->count * params->starts;
   const bool fork = b->classes.size() > 1;
   if (fork) QAP_CUDA(cudaEventRecord(b->fork, s));
   for (size_t k = 0; k < b->classes.size(); ++k) {
-    const BatchClass& c = b->classes[k];
+    BatchClass& c = b->classes[k];
     cudaStream_t cs = fork ? c.side : s;
+    if (b->timing && !c.t0) QAP_CUDA(cudaEventCreate(&c.t0));
+    if (b->timing && !c.t1) QAP_CUDA(cudaEventCreate(&c.t1));
     if (fork) QAP_CUDA(cudaStreamWaitEvent(cs, b->fork, 0));
     qapk::BatchArgs a{};
     a.insts = b->d_insts + (size_t)nt_index(c.plan.nt) * b->count;
@@ -792,13 +880,17 @@ qap_status qap_batch_search_async(qap_batch* b, const qap_search_params* params,
     a.items = c.items;
     a.counter = b->d_counter + k * kCounterStride;
     a.s = make_search_args(params, out, p_stride);
-    a.s.rws_off = delta_workspace(c.plan, b->dbytes);
+    a.s.rws_off = c.rws_off;
+    a.s.p_off = c.p_off;
     a.ws_stride = c.ws_stride;
     a.ws = c.ws_stride ? static_cast<unsigned char*>(b->ws) + c.ws_off : nullptr;
     QAP_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), cs));
     const auto fn = reinterpret_cast<qapk::BatchKernelFn>(const_cast<void*>(c.fn));
+    if (b->timing) QAP_CUDA(cudaEventRecord(c.t0, cs));
     fn<<<c.grid, c.plan.nt, c.smem, cs>>>(a);
     QAP_CUDA(cudaGetLastError());
+    if (b->timing) QAP_CUDA(cudaEventRecord(c.t1, cs));
+    c.timed = b->timing != 0;
     if (fork) {
       QAP_CUDA(cudaEventRecord(c.done, cs));
       QAP_CUDA(cudaStreamWaitEvent(s, c.done, 0));
@@ -812,7 +904,8 @@ qap_status qap_batch_search(qap_batch* b, const qap_search_params* params,
   if (!b) return QAP_EINVAL;
   QAP_TRY(validate_params(params));
   if (!out || !out->best_cost || p_stride < b->nmax) return QAP_EINVAL;
-  QAP_CUDA(cudaSetDevice(b->device));
+  DeviceGuard dg;
+  QAP_TRY(dg.set(b->device));
   const int W = b->count * params->starts;
   const OutLayout L = out_layout(W, p_stride);
   const size_t freq_off = (L.total + 255) / 256 * 256;
@@ -897,25 +990,36 @@ extern "C" qap_status qap_batch_search_noalloc(qap_batch* b, const qap_search_pa
     return QAP_EINVAL;
   }
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  QAP_CUDA(cudaSetDevice(b->device));
+  DeviceGuard dg;
+  QAP_TRY(dg.set(b->device));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // The tables are copied from static host memory that the next call
+  // overwrites; a captured copy would read it again at every replay.
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  QAP_CUDA(cudaStreamIsCapturing(s, &capturing));
+  if (capturing != cudaStreamCaptureStatusNone) {
+    snprintf(g_last_error, sizeof(g_last_error),
+             "qap_batch_search_noalloc: the stream is being captured; the call copies its "
+             "tables from host memory that the next call overwrites");
+    return QAP_EUNSUPPORTED;
+  }
   unsigned char* base = nullptr;
   QAP_TRY(noalloc_scratch(b->device, &base));
   Launch L;
   QAP_TRY(plan_batch(b, params, &L));
-  if (L.plan.store & (qapk::kGlobalDelta | qapk::kGlobalFlow)) {
+  if (ws_layout(L.plan, b->dbytes, b->fbytes, b->nmax, params).stride != 0) {
     snprintf(g_last_error, sizeof(g_last_error),
-             "qap_batch_search_noalloc: n = %d needs the large-n plan, whose workspace is "
-             "allocated; the no-allocation form holds n <= 181", b->nmax);
+             "qap_batch_search_noalloc: n = %d needs a plan with a per-CTA workspace, which is "
+             "allocated (the large-n plan, or int64 elements beyond shared memory)", b->nmax);
     return QAP_EUNSUPPORTED;
   }
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int count = b->count, W = params->starts;
 
   // instance table for this plan's thread count
   char* data = static_cast<char*>(b->data);
   for (int i = 0; i < count; ++i)
     g_noalloc_h_insts[i] = inst_args(b->di[i], data + b->offF[i], data + b->offFt[i],
-                                     reinterpret_cast<int8_t*>(data + b->offD[i]), L.plan.nt,
+                                     data + b->offD[i], L.plan.nt,
                                      b->fbytes);
   // items, longest instances first (stable counting sort by n)
   for (int v = 0; v <= kMaxN + 1; ++v) g_noalloc_h_bucket[v] = 0;

@@ -19,10 +19,12 @@ WalkKernelFn walk_kernel_i32_f8(int nt, int maxpt, int store);
 WalkKernelFn walk_kernel_i32_f8m(int nt, int maxpt, int store);
 WalkKernelFn walk_kernel_i32_f16(int nt, int maxpt, int store);
 WalkKernelFn walk_kernel_i64_f16(int nt, int maxpt, int store);
+WalkKernelFn walk_kernel_i64_f64(int nt, int maxpt, int store);
 BatchKernelFn batch_kernel_i32_f8(int nt, int maxpt, int store);
 BatchKernelFn batch_kernel_i32_f8m(int nt, int maxpt, int store);
 BatchKernelFn batch_kernel_i32_f16(int nt, int maxpt, int store);
 BatchKernelFn batch_kernel_i64_f16(int nt, int maxpt, int store);
+BatchKernelFn batch_kernel_i64_f64(int nt, int maxpt, int store);
 }  // namespace qapk
 
 namespace qaph {
@@ -53,7 +55,7 @@ inline constexpr int kMaxN = 256;
 struct Plan {
   int nt;
   int maxpt;
-  int store;  // 0, or qapk::kGlobalDelta [| qapk::kGlobalFlow] (large-n plans)
+  int store;  // qapk::kGlobalDelta, kGlobalFlow, kProductM, kGlobalP bits (0: all on chip)
 };
 
 // The large-n plan: 1024 threads, up to 40 slots each in a global workspace
@@ -112,36 +114,53 @@ inline int group_for(int n, int nt, int fbytes) {
 
 // One instance's shape on the device: F, F^T in `fbytes` elements with rows
 // of an odd number of 16-byte chunks (rows read side by side by the lanes of
-// a warp then fall in different banks), D as int8.
+// a warp then fall in different banks), D and P in `pbytes_of(fbytes)`.
 struct DevInstance {
   int n = 0, ldF = 0, ldP = 0, symF = 0, symD = 0;
   int64_t bound = 0;
   int64_t maxF = 0;
   int bytevec = 0;  // every difference of two F entries, and of two D entries, fits int8
+  int wide = 0;     // outside the narrow paths: int64 elements and arithmetic
 };
 
-// int8 flows (dp4a rows, and byte vectors for the O(1) update) when the
-// instance allows them and the deltas are int32; else int16 flows.
+// Largest bound of the int64 path.  With B = (n^2 + 8n + 32) max|F| max|D|
+// below 2^62, every cost (at most n^2 max|F| max|D|), delta, dot-product sum
+// and element product is below 2^62 in magnitude, and so is the difference
+// of two costs below 2^63 (the aspiration test compares a delta with it).
+inline constexpr int64_t kMaxBound = (int64_t)1 << 62;
+
+// Element width of F on the device: int8 (dp4a rows, byte vectors for the
+// O(1) update) when the instance allows it and the deltas are int32; int16
+// on the narrow path otherwise; 8 (int64 F, D and P) on the wide path.
 inline int flow_bytes(const DevInstance& di, int dbytes) {
+  if (di.wide) return 8;
   return (di.bytevec && dbytes == 4) ? 1 : 2;
 }
 
-inline int pad_ldF(int n, int fbytes) { return (16 / fbytes) * (((n * fbytes + 15) / 16) | 1); }
-inline int pad_ldP(int n) { return 16 * (((n + 15) / 16) | 1); }
+// P and D are int8 beside int8 or int16 flows and int64 beside int64 flows.
+inline int pbytes_of(int fbytes) { return fbytes == 8 ? 8 : 1; }
 
-// Checks ranges and symmetry of one instance.
+inline int pad_ldF(int n, int fbytes) { return (16 / fbytes) * (((n * fbytes + 15) / 16) | 1); }
+inline int pad_ldP(int n, int pbytes) { return (16 / pbytes) * (((n * pbytes + 15) / 16) | 1); }
+
+// Checks ranges and symmetry of one instance and picks its arithmetic:
+//  - narrow (int8 or int16 flows, int8 distances, 32-bit element sums) when
+//    F fits int16, D fits int8 and every dot product of two length-n rows
+//    pairs, 2 n max|F| max|D|, stays below 2^31;
+//  - wide (int64 elements and arithmetic) otherwise;
+//  - QAP_EOVERFLOW when B = (n^2 + 8n + 32) max|F| max|D| reaches 2^62.
 inline qap_status inspect_instance(const int64_t* F, const int64_t* D, int n, DevInstance* di) {
   if (!F || !D || n < 2) return QAP_EINVAL;
   if (n > kMaxN) return QAP_EUNSUPPORTED;
-  int64_t mF = 0, mD = 0;
+  uint64_t mF = 0, mD = 0;  // magnitudes (|INT64_MIN| included)
   int64_t loF = F[0], hiF = F[0], loD = D[0], hiD = D[0];
   int symF = 1, symD = 1;
+  auto mag = [](int64_t v) { return v < 0 ? (uint64_t)0 - (uint64_t)v : (uint64_t)v; };
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
       const int64_t f = F[(size_t)i * n + j], d = D[(size_t)i * n + j];
-      if (f < INT16_MIN || f > INT16_MAX || d < INT8_MIN || d > INT8_MAX) return QAP_EUNSUPPORTED;
-      mF = std::max<int64_t>(mF, f < 0 ? -f : f);
-      mD = std::max<int64_t>(mD, d < 0 ? -d : d);
+      mF = std::max(mF, mag(f));
+      mD = std::max(mD, mag(d));
       loF = std::min(loF, f);
       hiF = std::max(hiF, f);
       loD = std::min(loD, d);
@@ -149,13 +168,20 @@ inline qap_status inspect_instance(const int64_t* F, const int64_t* D, int n, De
       if (f != F[(size_t)j * n + i]) symF = 0;
       if (d != D[(size_t)j * n + i]) symD = 0;
     }
-  const int64_t nn = n;
+  const unsigned __int128 nn = (unsigned)n;
+  const unsigned __int128 B = (nn * nn + 8 * nn + 32) * (unsigned __int128)mF * mD;
+  if (B >= (unsigned __int128)kMaxBound) return QAP_EOVERFLOW;
+  const bool in16 = loF >= INT16_MIN && hiF <= INT16_MAX && loD >= INT8_MIN && hiD <= INT8_MAX;
+  const unsigned __int128 dots = 2 * nn * (unsigned __int128)mF * mD;
   di->n = n;
   di->symF = symF;
   di->symD = symD;
-  di->bound = (nn * nn + 8 * nn + 32) * mF * mD;  // < 2^40 for n <= 181
-  di->maxF = mF;
-  di->bytevec = mF <= 127 && hiF - loF <= 127 && hiD - loD <= 127;
+  di->bound = (int64_t)B;
+  di->maxF = (int64_t)mF;
+  di->wide = !(in16 && dots <= (unsigned __int128)INT32_MAX);
+  // differences of two F entries and of two D entries fit a byte (no
+  // overflow here: on this branch the ranges fit int16 and int8)
+  di->bytevec = !di->wide && mF <= 127 && hiF - loF <= 127 && hiD - loD <= 127;
   return QAP_OK;
 }
 
@@ -164,20 +190,28 @@ inline void build_images(const int64_t* F, const int64_t* D, const DevInstance& 
                   std::vector<unsigned char>& img_F, std::vector<unsigned char>& img_Ft,
                   std::vector<unsigned char>& img_D) {
   const int n = di.n, ld = di.ldF;
+  const int pbytes = pbytes_of(fbytes);
   img_F.assign((size_t)n * ld * fbytes, 0);
   img_Ft.assign((size_t)n * ld * fbytes, 0);
-  img_D.resize((size_t)n * n);
+  img_D.resize((size_t)n * n * pbytes);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
       const int64_t f = F[(size_t)i * n + j];
       if (fbytes == 1) {
         reinterpret_cast<int8_t*>(img_F.data())[(size_t)i * ld + j] = (int8_t)f;
         reinterpret_cast<int8_t*>(img_Ft.data())[(size_t)j * ld + i] = (int8_t)f;
-      } else {
+      } else if (fbytes == 2) {
         reinterpret_cast<int16_t*>(img_F.data())[(size_t)i * ld + j] = (int16_t)f;
         reinterpret_cast<int16_t*>(img_Ft.data())[(size_t)j * ld + i] = (int16_t)f;
+      } else {
+        reinterpret_cast<int64_t*>(img_F.data())[(size_t)i * ld + j] = f;
+        reinterpret_cast<int64_t*>(img_Ft.data())[(size_t)j * ld + i] = f;
       }
-      img_D[(size_t)i * n + j] = (unsigned char)(int8_t)D[(size_t)i * n + j];
+      const int64_t d = D[(size_t)i * n + j];
+      if (pbytes == 1)
+        img_D[(size_t)i * n + j] = (unsigned char)(int8_t)d;
+      else
+        reinterpret_cast<int64_t*>(img_D.data())[(size_t)i * n + j] = d;
     }
 }
 
@@ -189,12 +223,14 @@ inline qap_status device_attrs(int* device, int* sms, int* smem_optin) {
 }
 
 inline qapk::WalkKernelFn pick_walk_kernel(int dbytes, int fbytes, const Plan& p) {
+  if (fbytes == 8) return qapk::walk_kernel_i64_f64(p.nt, p.maxpt, p.store);
   if (dbytes == 8) return qapk::walk_kernel_i64_f16(p.nt, p.maxpt, p.store);
   if (fbytes == 1) return qapk::walk_kernel_i32_f8(p.nt, p.maxpt, p.store);
   return qapk::walk_kernel_i32_f16(p.nt, p.maxpt, p.store);
 }
 
 inline qapk::BatchKernelFn pick_batch_kernel(int dbytes, int fbytes, const Plan& p) {
+  if (fbytes == 8) return qapk::batch_kernel_i64_f64(p.nt, p.maxpt, p.store);
   if (dbytes == 8) return qapk::batch_kernel_i64_f16(p.nt, p.maxpt, p.store);
   if (fbytes == 1) return qapk::batch_kernel_i32_f8(p.nt, p.maxpt, p.store);
   return qapk::batch_kernel_i32_f16(p.nt, p.maxpt, p.store);
@@ -231,6 +267,17 @@ inline Plan with_products(Plan p, const DevInstance* d, int count, int fbytes, i
   return plan_smem(m, d, count, fbytes, dbytes) + reserve <= smem_optin ? m : p;
 }
 
+// The int64 element path reads F and F^T from global memory (L1-cached,
+// read-only), and keeps P and P^T in the CTA's workspace too when they do
+// not fit shared memory.
+inline Plan wide_store(Plan p, const DevInstance* d, int count, int fbytes, int dbytes,
+                       int smem_optin, int reserve) {
+  if (fbytes != 8) return p;
+  p.store |= qapk::kGlobalFlow;
+  if (plan_smem(p, d, count, fbytes, dbytes) + reserve > smem_optin) p.store |= qapk::kGlobalP;
+  return p;
+}
+
 // A register plan when one holds n and fits shared memory (in its products
 // form when that fits as well); else the large-n plan, with F in global
 // memory when it does not fit shared memory either.  `many`: the launch has
@@ -240,38 +287,51 @@ inline Plan with_products(Plan p, const DevInstance* d, int count, int fbytes, i
 inline bool choose_plan_fit(int nmax, int threads, bool many, const DevInstance* d, int count,
                             int fbytes, int dbytes, int smem_optin, int reserve, Plan* out) {
   Plan p;
-  if (nmax <= 181 && choose_plan(nmax, threads, many, &p) &&
-      plan_smem(p, d, count, fbytes, dbytes) + reserve <= smem_optin) {
-    Plan m = with_products(p, d, count, fbytes, dbytes, smem_optin, reserve);
-    if (many && threads == 0 && p.nt == 256 && p.maxpt > 8) {
-      // two CTAs per SM: each with its own 1 KB reserved by the hardware
-      auto two = [&](const Plan& x) {
-        return 2 * (plan_smem(x, d, count, fbytes, dbytes) + reserve + 1024) <= smem_optin + 1024;
-      };
-      if (!two(m)) m = p;
-      if (!two(m))
-        return choose_plan_fit(nmax, threads, false, d, count, fbytes, dbytes, smem_optin,
-                               reserve, out);
+  if (nmax <= 181 && choose_plan(nmax, threads, many, &p)) {
+    p = wide_store(p, d, count, fbytes, dbytes, smem_optin, reserve);
+    if (plan_smem(p, d, count, fbytes, dbytes) + reserve <= smem_optin) {
+      Plan m = with_products(p, d, count, fbytes, dbytes, smem_optin, reserve);
+      if (many && threads == 0 && p.nt == 256 && p.maxpt > 8) {
+        // two CTAs per SM: each with its own 1 KB reserved by the hardware
+        auto two = [&](const Plan& x) {
+          return 2 * (plan_smem(x, d, count, fbytes, dbytes) + reserve + 1024) <=
+                 smem_optin + 1024;
+        };
+        if (!two(m)) m = p;
+        if (!two(m))
+          return choose_plan_fit(nmax, threads, false, d, count, fbytes, dbytes, smem_optin,
+                                 reserve, out);
+      }
+      *out = m;
+      return true;
     }
-    *out = m;
-    return true;
   }
   if (threads != 0 && threads != kLargePlan.nt) return false;
   if (qapk::row_segments(nmax, kLargePlan.maxpt) > kLargePlan.nt) return false;
   p = kLargePlan;
-  if (plan_smem(p, d, count, fbytes, dbytes) + reserve > smem_optin)
+  if (fbytes == 8)
+    p = wide_store(p, d, count, fbytes, dbytes, smem_optin, reserve);
+  else if (plan_smem(p, d, count, fbytes, dbytes) + reserve > smem_optin)
     p.store |= qapk::kGlobalFlow;
   if (plan_smem(p, d, count, fbytes, dbytes) + reserve > smem_optin) return false;
   *out = p;
   return true;
 }
 
-// Per-CTA workspace: the deltas and marks of large-n plans, then the tables
-// of the other tabu criteria and of the frequency penalty when a search
-// uses them (loc_until n x n, unit_until n, applied n x n; int32).
+// Per-CTA workspace: the deltas and marks of large-n plans, then P and P^T
+// of kGlobalP plans (sized for the largest n), then the tables of the other
+// tabu criteria and of the frequency penalty when a search uses them
+// (loc_until n x n, unit_until n, applied n x n; int32).
 inline size_t delta_workspace(const Plan& p, int dbytes) {
   if (!(p.store & qapk::kGlobalDelta)) return 0;
   const size_t b = (size_t)p.nt * p.maxpt * ((size_t)dbytes + 4);
+  return (b + 255) / 256 * 256;
+}
+
+inline size_t p_workspace(const Plan& p, int fbytes, int nmax) {
+  if (!(p.store & qapk::kGlobalP)) return 0;
+  const int pb = pbytes_of(fbytes);
+  const size_t b = 2 * (size_t)nmax * pad_ldP(nmax, pb) * pb;
   return (b + 255) / 256 * 256;
 }
 
@@ -279,40 +339,86 @@ inline bool uses_rule_tables(const qap_search_params* sp) {
   return sp->iters > 0 && (sp->criterion != QAP_TABU_PAIR || sp->freq_penalty != 0);
 }
 
-inline size_t workspace_per_cta(const Plan& p, int dbytes, int nmax,
-                                const qap_search_params* sp) {
-  size_t b = delta_workspace(p, dbytes);
-  if (uses_rule_tables(sp)) b += ((size_t)(2 * nmax * nmax + nmax) * 4 + 255) / 256 * 256;
-  return b;
+struct WsLayout {
+  size_t p_off;    // P, P^T (kGlobalP plans)
+  size_t rws_off;  // tables of the other criteria and of the penalty
+  size_t stride;   // bytes per CTA (0: no workspace)
+};
+
+inline WsLayout ws_layout(const Plan& p, int dbytes, int fbytes, int nmax,
+                          const qap_search_params* sp) {
+  WsLayout w;
+  w.p_off = delta_workspace(p, dbytes);
+  w.rws_off = w.p_off + p_workspace(p, fbytes, nmax);
+  w.stride = w.rws_off;
+  if (uses_rule_tables(sp)) w.stride += ((size_t)(2 * nmax * nmax + nmax) * 4 + 255) / 256 * 256;
+  return w;
 }
 
 // With the frequency penalty a non-improving move's rank is delta + lambda *
-// count, count <= iters; int32 deltas must hold it below their sentinel.
+// count, count <= iters; int32 deltas must hold it below their sentinel, int64
+// deltas below the int64 path's bound.
 inline qap_status check_penalty(const qap_search_params* sp, int dbytes, int64_t bound) {
-  if (sp->freq_penalty == 0 || sp->iters == 0 || dbytes == 8) return QAP_OK;
-  const int64_t top = bound + (int64_t)sp->freq_penalty * sp->iters;
+  if (sp->freq_penalty == 0 || sp->iters == 0) return QAP_OK;
+  const int64_t top = bound + (int64_t)sp->freq_penalty * sp->iters;  // < 2^62 + 2^62
+  if (dbytes == 8) return top < kMaxBound ? QAP_OK : QAP_EOVERFLOW;
   return top < (int64_t)INT32_MAX - 1 ? QAP_OK : QAP_EOVERFLOW;
 }
 
 extern std::mutex g_attr_mu;
 
+// Makes a device current for the length of an entry point and gives the
+// caller's current device back on return, so that a call never leaves the
+// calling thread on another device.
+class DeviceGuard {
+ public:
+  DeviceGuard() = default;
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+  qap_status set(int device) {
+    QAP_CUDA(cudaGetDevice(&prev_));
+    if (prev_ != device) {
+      QAP_CUDA(cudaSetDevice(device));
+      changed_ = true;
+    }
+    return QAP_OK;
+  }
+  ~DeviceGuard() {
+    if (changed_) cudaSetDevice(prev_);
+  }
+
+ private:
+  int prev_ = 0;
+  bool changed_ = false;
+};
+
+// Kernels whose dynamic shared-memory limit has been raised, per device: a
+// fixed table, so that the check allocates nothing.  When it is full the
+// attribute is simply set again on every launch (an idempotent call).
+inline constexpr int kPreparedMax = 1024;
+struct PreparedKernel {
+  const void* fn;
+  int device;
+};
+extern PreparedKernel g_prepared[kPreparedMax];
+extern int g_prepared_count;
+
 inline qap_status prepare_kernel(const void* fn, int smem) {
   // The dynamic shared-memory limit is a property of the function, shared
   // by every launch of it from any thread; raise it once to the device
   // maximum so that no launch can find it lowered by a smaller request.
-  static std::vector<const void*> done;
   std::lock_guard<std::mutex> lk(g_attr_mu);
-  for (const void* f : done)
-    if (f == fn) return QAP_OK;
   int dev = 0, optin = 0;
   QAP_CUDA(cudaGetDevice(&dev));
+  for (int i = 0; i < g_prepared_count; ++i)
+    if (g_prepared[i].fn == fn && g_prepared[i].device == dev) return QAP_OK;
   QAP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   cudaFuncAttributes fa{};
   QAP_CUDA(cudaFuncGetAttributes(&fa, fn));
   const int dyn_max = optin - (int)fa.sharedSizeBytes;  // the static part counts too
   if (smem > dyn_max) return QAP_EUNSUPPORTED;
   QAP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
-  done.push_back(fn);
+  if (g_prepared_count < kPreparedMax) g_prepared[g_prepared_count++] = PreparedKernel{fn, dev};
   return QAP_OK;
 }
 
@@ -445,8 +551,8 @@ inline qap_status copy_outputs_back(const qap_walk_outputs* out, const qap_walk_
   return QAP_OK;
 }
 
-inline qapk::InstArgs inst_args(const DevInstance& d, const void* F, const void* Ft, const int8_t* D,
-                         int nt, int fbytes) {
+inline qapk::InstArgs inst_args(const DevInstance& d, const void* F, const void* Ft, const void* D,
+                                int nt, int fbytes) {
   qapk::InstArgs I{};
   I.n = d.n;
   I.ldF = d.ldF;

@@ -54,12 +54,12 @@ constexpr int kDescentCap = 1 << 20;      // 2opt moves when no cap is given
 
 // One instance as the kernels see it.
 struct InstArgs {
-  int n, ldF, ldP;    // ldF: elements per F row; ldP: bytes per P row
+  int n, ldF, ldP;    // ldF: elements per F row; ldP: elements per P row
   int symF, symD;
   int group;          // lanes per phase-X task (1, 2, 4 or 8)
-  const void* F;      // n x ldF (int8 or int16), row-major, zero padded
+  const void* F;      // n x ldF (int8, int16 or int64), row-major, zero padded
   const void* Ft;     // transpose of F (== F when symF)
-  const int8_t* D;    // n x n, row-major
+  const void* D;      // n x n, row-major (int8, or int64 with int64 flows)
 };
 
 // Search parameters and per-walk outputs (rows indexed by output row).
@@ -72,6 +72,7 @@ struct SearchArgs {
   int crit;           // tabu criterion: 0 pair (r, s), 1 unit-location, 2 unit
   int lambda;         // frequency penalty on non-improving moves (0 = off)
   size_t rws_off;     // offset of the criterion/penalty tables in a CTA's workspace
+  size_t p_off;       // offset of P (then P^T) in a CTA's workspace (kGlobalP plans)
   int p_stride;       // elements per best_p row
   int32_t* best_p;
   int64_t* best_cost;
@@ -124,6 +125,10 @@ constexpr int kGlobalFlow = 2;
 // in shared memory and update them after each move (see phase_m_update),
 // so that phase X reads the dot products it needs instead of computing them.
 constexpr int kProductM = 4;
+// Plans with bit kGlobalP (int64 elements only) keep P and P^T in the CTA's
+// workspace (at SearchArgs::p_off) instead of shared memory; they read F and
+// F^T from global memory too.
+constexpr int kGlobalP = 8;
 
 // row stride of M in int32 words: whole 16-byte groups, an odd number of
 // them (rows read side by side by consecutive threads spread over banks)
@@ -140,19 +145,24 @@ struct SmemLayout {
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
+// fbytes: bytes per F element (1, 2, or 8 for the int64 element path, whose
+// P and update vectors are int64 too)
 __host__ __device__ inline SmemLayout smem_layout(int n, int ldF, int fbytes, int ldP, int symF,
                                                   int symD, int dbytes, int slots,
                                                   int store = 0) {
   SmemLayout L;
   int o = 0;
   const bool fg = store & kGlobalFlow;
+  const bool pg = store & kGlobalP;
+  const int pbytes = fbytes == 8 ? 8 : 1;   // P element
+  const int vbytes = fbytes == 8 ? 32 : 16; // update vector (a, b, c, e) of one index
   if (store & kGlobalDelta) slots = 0;
   L.offF = o;    o = fg ? o : align16(o + n * ldF * fbytes);
   L.offFt = o;   o = (symF || fg) ? o : align16(o + n * ldF * fbytes);
-  L.offP = o;    o = align16(o + n * ldP);
-  L.offPt = o;   o = symD ? o : align16(o + n * ldP);
+  L.offP = o;    o = pg ? o : align16(o + n * ldP * pbytes);
+  L.offPt = o;   o = (symD || pg) ? o : align16(o + n * ldP * pbytes);
   L.offTabu = o; o = align16(o + slots * 4);
-  L.offVec = o;  o = align16(o + n * 16);
+  L.offVec = o;  o = align16(o + n * vbytes);
   L.offR = o;    o = align16(o + 2 * n * dbytes);
   L.offG0 = o;   o = align16(o + n * dbytes);
   L.offG1 = o;   o = align16(o + n * dbytes);
@@ -173,6 +183,18 @@ template <> struct DeltaMax<int64_t> { static constexpr int64_t v = LLONG_MAX; }
 template <typename DT> struct DeltaMin;
 template <> struct DeltaMin<int32_t> { static constexpr int32_t v = INT_MIN; };
 template <> struct DeltaMin<int64_t> { static constexpr int64_t v = LLONG_MIN; };
+
+// Element types: F is stored as FE, P (and D) as Elem<FE>::P; differences,
+// products and dot-product sums of elements are Elem<FE>::S.  The narrow
+// paths (int8 or int16 flows, int8 distances) keep S in 32 bits: the host
+// admits an instance to them only when every such sum fits, 2 n max|F|
+// max|D| < 2^31.  The wide path stores F and D as int64 and computes in
+// int64; the host admits it while the cost bound stays below 2^62, so that
+// no sum, delta or cost difference leaves int64.
+template <typename FE> struct Elem;
+template <> struct Elem<int8_t> { using P = int8_t; using S = int; };
+template <> struct Elem<int16_t> { using P = int8_t; using S = int; };
+template <> struct Elem<int64_t> { using P = int64_t; using S = int64_t; };
 
 // ---------------------------------------------------------------------------
 // row chunks: F rows as int8 (16 per chunk, dp4a) or int16 (8, dp2a)
@@ -200,6 +222,16 @@ template <> struct Chunk<int16_t> {
     acc = __dp2a_hi(f.y, q.x, acc);
     acc = __dp2a_lo(f.z, q.y, acc);
     return __dp2a_hi(f.w, q.y, acc);
+  }
+};
+
+// int64 flows and distances: two elements per 16-byte chunk
+template <> struct Chunk<int64_t> {
+  static constexpr int W = 2;
+  using FV = longlong2;
+  using QV = longlong2;
+  __device__ __forceinline__ static int64_t dot(const FV f, const QV q, int64_t acc) {
+    return acc + f.x * q.x + f.y * q.y;
   }
 };
 
@@ -247,6 +279,24 @@ template <> struct VecOps<int16_t> {
   template <typename DT>
   __device__ __forceinline__ static DT update(const U& u, const V v, DT d) {
     return d + (DT)((u.x - v.x) * (u.y - v.y) + (u.z - v.z) * (u.w - v.w));
+  }
+};
+
+// int64 elements: (a, b, c, e) as four int64 in 32 bytes
+struct alignas(16) Vec64 {
+  long long a, b, c, e;
+};
+
+template <> struct VecOps<int64_t> {
+  using V = Vec64;
+  using U = Vec64;
+  __device__ __forceinline__ static V pack(int64_t a, int64_t b, int64_t c, int64_t e) {
+    return V{a, b, c, e};
+  }
+  __device__ __forceinline__ static U prep(const V u) { return u; }
+  template <typename DT>
+  __device__ __forceinline__ static DT update(const U& u, const V v, DT d) {
+    return d + (DT)((u.a - v.a) * (u.b - v.b) + (u.c - v.c) * (u.e - v.e));
   }
 };
 
@@ -310,8 +360,8 @@ template <typename DT, typename FE>
 struct WalkSmem {
   FE* F;
   FE* Ft;
-  int8_t* P;
-  int8_t* Pt;
+  typename Elem<FE>::P* P;
+  typename Elem<FE>::P* Pt;
   int32_t* tabu;
   void* vec;  // VecOps<FE>::V per index
   DT* R;
@@ -331,27 +381,29 @@ struct WalkSmem {
 template <typename DT, typename FE>
 __device__ __forceinline__ DT delta_serial(const WalkSmem<DT, FE>& S, int n, int ldF, int ldP,
                                            bool sym, int x, int k) {
+  using PE = typename Elem<FE>::P;
+  using SC = typename Elem<FE>::S;
   const FE* Fx = S.F + x * ldF;
   const FE* Fk = S.F + k * ldF;
-  const int8_t* Px = S.P + x * ldP;
-  const int8_t* Pk = S.P + k * ldP;
+  const PE* Px = S.P + x * ldP;
+  const PE* Pk = S.P + k * ldP;
   const FE* Ftx = S.Ft + x * ldF;
   const FE* Ftk = S.Ft + k * ldF;
-  const int8_t* Ptx = S.Pt + x * ldP;
-  const int8_t* Ptk = S.Pt + k * ldP;
+  const PE* Ptx = S.Pt + x * ldP;
+  const PE* Ptk = S.Pt + k * ldP;
   DT acc = 0;
   for (int j = 0; j < n; ++j) {
     if (j == x || j == k) continue;
-    const int t1 = ((int)Fx[j] - (int)Fk[j]) * ((int)Pk[j] - (int)Px[j]);
+    const SC t1 = ((SC)Fx[j] - (SC)Fk[j]) * ((SC)Pk[j] - (SC)Px[j]);
     if (sym) {
       acc += (DT)(2 * t1);
     } else {
-      const int t2 = ((int)Ftx[j] - (int)Ftk[j]) * ((int)Ptk[j] - (int)Ptx[j]);
+      const SC t2 = ((SC)Ftx[j] - (SC)Ftk[j]) * ((SC)Ptk[j] - (SC)Ptx[j]);
       acc += (DT)t1 + (DT)t2;
     }
   }
-  const int fixed = ((int)Fx[k] - (int)Fk[x]) * ((int)Pk[x] - (int)Px[k]);
-  const int diag = ((int)Fx[x] - (int)Fk[k]) * ((int)Pk[k] - (int)Px[x]);
+  const SC fixed = ((SC)Fx[k] - (SC)Fk[x]) * ((SC)Pk[x] - (SC)Px[k]);
+  const SC diag = ((SC)Fx[x] - (SC)Fk[k]) * ((SC)Pk[k] - (SC)Px[x]);
   return acc + (DT)fixed + (DT)diag;
 }
 
@@ -370,7 +422,7 @@ __device__ __forceinline__ void compute_g(const WalkSmem<DT, FE>& S, DT* g, int 
     const auto* Pk = reinterpret_cast<const typename C::QV*>(S.P + k * ldP);
     const auto* Ftk = reinterpret_cast<const typename C::FV*>(S.Ft + k * ldF);
     const auto* Ptk = reinterpret_cast<const typename C::QV*>(S.Pt + k * ldP);
-    int acc = 0;
+    typename Elem<FE>::S acc = 0;
     for (int c = lg; c < nc; c += G) {
       acc = C::dot(Fk[c], Pk[c], acc);
       if (!sym) acc = C::dot(Ftk[c], Ptk[c], acc);
@@ -393,14 +445,16 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
   using FV = typename C::FV;
   using QV = typename C::QV;
   using VO = VecOps<FE>;
+  using PE = typename Elem<FE>::P;
+  using SC = typename Elem<FE>::S;
   const int lg = threadIdx.x & (G - 1);
   const int grp = threadIdx.x / G;
   const int NG = NT / G;
   const int nc = (n + C::W - 1) / C::W;
   const FE* F = S.F;
-  const int8_t* Q = S.P;
+  const PE* Q = S.P;
   const FE* Ft = S.Ft;
-  const int8_t* Qt = S.Pt;
+  const PE* Qt = S.Pt;
   const FV* Fr = reinterpret_cast<const FV*>(F + r * ldF);
   const FV* Fs = reinterpret_cast<const FV*>(F + s * ldF);
   const FV* Ftr = reinterpret_cast<const FV*>(Ft + r * ldF);
@@ -410,10 +464,10 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
   const QV* Qtr = reinterpret_cast<const QV*>(Qt + r * ldP);
   const QV* Qts = reinterpret_cast<const QV*>(Qt + s * ldP);
   // 2x2 blocks of F and Q at {r, s}
-  const int fRR = F[r * ldF + r], fRS = F[r * ldF + s];
-  const int fSR = F[s * ldF + r], fSS = F[s * ldF + s];
-  const int qRR = Q[r * ldP + r], qRS = Q[r * ldP + s];
-  const int qSR = Q[s * ldP + r], qSS = Q[s * ldP + s];
+  const SC fRR = F[r * ldF + r], fRS = F[r * ldF + s];
+  const SC fSR = F[s * ldF + r], fSS = F[s * ldF + s];
+  const SC qRR = Q[r * ldP + r], qRS = Q[r * ldP + s];
+  const SC qSR = Q[s * ldP + r], qSS = Q[s * ldP + s];
   // Up to 512 threads the bound is the same for every lane of a warp (its
   // first group), so whole warps run each round and the reductions use
   // full-warp shuffles; lanes past n work on row n - 1 and store nothing.
@@ -433,7 +487,7 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
     const int kq = gt ? (k == r ? s : r) : k;
     // scalars of the finish; loaded before the dots so their latency hides
     // under them, except at 1024 threads, whose 64 registers cannot hold them
-    struct Fin { int Frk, Fsk, Fkr, Fks, Qrk, Qsk, Qkr, Qks, Fkk, Qkk; DT gck; };
+    struct Fin { SC Frk, Fsk, Fkr, Fks, Qrk, Qsk, Qkr, Qks, Fkk, Qkk; DT gck; };
     auto load_fin = [&]() {
       return Fin{F[r * ldF + k],  F[s * ldF + k],  Ft[r * ldF + k], Ft[s * ldF + k],
                  Q[r * ldP + k],  Q[s * ldP + k],  Qt[r * ldP + k], Qt[s * ldP + k],
@@ -446,7 +500,7 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
     const FV* Ftk = reinterpret_cast<const FV*>(Ft + kq * ldF);
     const QV* Qk = reinterpret_cast<const QV*>(Q + kq * ldP);
     const QV* Qtk = reinterpret_cast<const QV*>(Qt + kq * ldP);
-    int Ar = 0, Br = 0, As = 0, Bs = 0;
+    SC Ar = 0, Br = 0, As = 0, Bs = 0;
     if (sym) {
       for (int c = lg; c < nc; c += G) {
         const FV fk = Fk[c];
@@ -472,7 +526,7 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
     }
     // reduce-scatter: even lanes gather (Ar, Br), odd lanes (As, Bs)
     const bool odd = lg & 1;
-    int A = odd ? As : Ar, B = odd ? Bs : Br;
+    SC A = odd ? As : Ar, B = odd ? Bs : Br;
     if (G > 1) {
       A += __shfl_xor_sync(smask, odd ? Ar : As, 1);
       B += __shfl_xor_sync(smask, odd ? Br : Bs, 1);
@@ -487,36 +541,36 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
       //           + (F[r][x]-F[s][x])(Q[s][xb]-Q[r][xb])
       const bool xs = (k == s);
       if (lg != ((G > 1 && xs) ? 1 : 0)) continue;  // the lane holding Ar or As
-      const int A0 = (G > 1) ? A : (xs ? As : Ar);
-      const int c1 = (xs ? fSR - fSS : fRR - fRS) * (xs ? qRS - qRR : qSS - qSR);
-      const int c2 = (xs ? fRS - fSS : fRR - fSR) * (xs ? qSR - qRR : qSS - qRS);
+      const SC A0 = (G > 1) ? A : (xs ? As : Ar);
+      const SC c1 = (xs ? fSR - fSS : fRR - fRS) * (xs ? qRS - qRR : qSS - qSR);
+      const SC c2 = (xs ? fRS - fSS : fRR - fSR) * (xs ? qSR - qRR : qSS - qRS);
       gn[k] = sym ? (DT)2 * ((DT)A0 + (DT)c1) : (DT)A0 + (DT)c1 + (DT)c2;
       continue;
     }
     if constexpr (!kEarly) fin = load_fin();
-    const int Frk = fin.Frk, Fsk = fin.Fsk, Fkr = fin.Fkr, Fks = fin.Fks;
-    const int Qrk = fin.Qrk, Qsk = fin.Qsk, Qkr = fin.Qkr, Qks = fin.Qks;
-    const int Fkk = fin.Fkk, Qkk = fin.Qkk;
-    const int a = Frk - Fsk, b = Qrk - Qsk, c = Fkr - Fks, e = Qkr - Qks;
+    const SC Frk = fin.Frk, Fsk = fin.Fsk, Fkr = fin.Fkr, Fks = fin.Fks;
+    const SC Qrk = fin.Qrk, Qsk = fin.Qsk, Qkr = fin.Qkr, Qks = fin.Qks;
+    const SC Fkk = fin.Fkk, Qkk = fin.Qkk;
+    const SC a = Frk - Fsk, b = Qrk - Qsk, c = Fkr - Fks, e = Qkr - Qks;
     const DT gk = fin.gck - (DT)(a * b) - (DT)(c * e);
     for (int xi = lg; xi < 2; xi += (G == 1 ? 1 : 2)) {
       const bool xs = xi != 0;
-      const int fxx = xs ? fSS : fRR;   // F[x][x]
-      const int pxx = xs ? qRR : qSS;   // P'[x][x] = Q[xb][xb]
-      const int fxk = xs ? Fsk : Frk;   // F[x][k]
-      const int fkx = xs ? Fks : Fkr;   // F[k][x]
-      const int pxk = xs ? Qrk : Qsk;   // P'[x][k] = Q[xb][k]
-      const int pkx = xs ? Qkr : Qks;   // P'[k][x] = Q[k][xb]
+      const SC fxx = xs ? fSS : fRR;   // F[x][x]
+      const SC pxx = xs ? qRR : qSS;   // P'[x][x] = Q[xb][xb]
+      const SC fxk = xs ? Fsk : Frk;   // F[x][k]
+      const SC fkx = xs ? Fks : Fkr;   // F[k][x]
+      const SC pxk = xs ? Qrk : Qsk;   // P'[x][k] = Q[xb][k]
+      const SC pkx = xs ? Qkr : Qks;   // P'[k][x] = Q[k][xb]
       // exchanged columns: (F[x][r]-F[x][s]), (F[r][x]-F[s][x]),
       // (Q[xb][s]-Q[xb][r]), (Q[s][xb]-Q[r][xb])
-      const int fx_rs = xs ? fSR - fSS : fRR - fRS;
-      const int frs_x = xs ? fRS - fSS : fRR - fSR;
-      const int qxb_sr = xs ? qRS - qRR : qSS - qSR;
-      const int qsr_xb = xs ? qSR - qRR : qSS - qRS;
-      const int corr = (fxx - fxk - fkx + Fkk) * (pxx - pxk - pkx + Qkk);
-      const int sig = -fx_rs * e - frs_x * b + qxb_sr * c + qsr_xb * a;
-      const int Ax = (G > 1) ? A : (xs ? As : Ar);
-      const int Bx = (G > 1) ? B : (xs ? Bs : Br);
+      const SC fx_rs = xs ? fSR - fSS : fRR - fRS;
+      const SC frs_x = xs ? fRS - fSS : fRR - fSR;
+      const SC qxb_sr = xs ? qRS - qRR : qSS - qSR;
+      const SC qsr_xb = xs ? qSR - qRR : qSS - qRS;
+      const SC corr = (fxx - fxk - fkx + Fkk) * (pxx - pxk - pkx + Qkk);
+      const SC sig = -fx_rs * e - frs_x * b + qxb_sr * c + qsr_xb * a;
+      const SC Ax = (G > 1) ? A : (xs ? As : Ar);
+      const SC Bx = (G > 1) ? B : (xs ? Bs : Br);
       const DT cross = sym ? (DT)2 * ((DT)Ax + (DT)Bx) : (DT)Ax + (DT)Bx;
       S.R[xi * n + k] = cross + (DT)sig - gk + (DT)corr;
     }
@@ -667,9 +721,9 @@ __device__ __forceinline__ void phase_m_update(const int32_t* Mc, int32_t* Mn, c
 // the other rows: one thread per (matrix, row); rows r and s: 4-byte words by
 // the last warp (lanes 0-15 for P, 16-31 for P^T), whose lanes then exchange
 // the entries r and s inside those two rows.
-template <int NT>
-__device__ __forceinline__ void swap_rs(int8_t* P, int8_t* Pt, int32_t* perm, int n, int ldP,
-                                        bool symD, int r, int s) {
+template <int NT, typename PE>
+__device__ __forceinline__ void swap_rs(PE* P, PE* Pt, int32_t* perm, int n, int ldP, bool symD,
+                                        int r, int s) {
   const int tid = threadIdx.x;
   if (tid == 0) {
     const int32_t t = perm[r];
@@ -680,18 +734,19 @@ __device__ __forceinline__ void swap_rs(int8_t* P, int8_t* Pt, int32_t* perm, in
   for (int c = tid; c < mats * n; c += NT) {
     const int j = c < n ? c : c - n;
     if (j == r || j == s) continue;
-    int8_t* Pj = (c < n ? P : Pt) + j * ldP;
-    const int8_t t = Pj[r];
+    PE* Pj = (c < n ? P : Pt) + j * ldP;
+    const PE t = Pj[r];
     Pj[r] = Pj[s];
     Pj[s] = t;
   }
   if (tid >= NT - 32) {
     const int lane = tid & 31, m = lane >> 4, l = lane & 15;
     if (m < mats) {
-      int8_t* M = m ? Pt : P;
+      PE* M = m ? Pt : P;
       int32_t* Mr = reinterpret_cast<int32_t*>(M + r * ldP);
       int32_t* Ms = reinterpret_cast<int32_t*>(M + s * ldP);
-      for (int w = l; w < (n + 3) / 4; w += 16) {
+      const int words = (n * (int)sizeof(PE) + 3) / 4;
+      for (int w = l; w < words; w += 16) {
         const int32_t a = Mr[w];
         Mr[w] = Ms[w];
         Ms[w] = a;
@@ -699,10 +754,10 @@ __device__ __forceinline__ void swap_rs(int8_t* P, int8_t* Pt, int32_t* perm, in
     }
     __syncwarp();
     if (l == 0 && m < mats) {
-      int8_t* M = m ? Pt : P;
-      int8_t* Rr = M + r * ldP;
-      int8_t* Rs = M + s * ldP;
-      int8_t t = Rr[r]; Rr[r] = Rr[s]; Rr[s] = t;
+      PE* M = m ? Pt : P;
+      PE* Rr = M + r * ldP;
+      PE* Rs = M + s * ldP;
+      PE t = Rr[r]; Rr[r] = Rr[s]; Rr[s] = t;
       t = Rs[r]; Rs[r] = Rs[s]; Rs[s] = t;
     }
   }
@@ -764,7 +819,8 @@ __device__ __forceinline__ Segment make_segment(int n) {
 
 template <typename DT, typename FE, int NT, int MAXPT, int STORE>
 __device__ __forceinline__ WalkSmem<DT, FE> smem_views(unsigned char* smem, const InstArgs& I,
-                                                       unsigned char* ws) {
+                                                       unsigned char* ws, size_t p_off) {
+  using PE = typename Elem<FE>::P;
   const SmemLayout L = smem_layout(I.n, I.ldF, (int)sizeof(FE), I.ldP, I.symF, I.symD,
                                    (int)sizeof(DT), NT * MAXPT, STORE);
   WalkSmem<DT, FE> S;
@@ -775,8 +831,13 @@ __device__ __forceinline__ WalkSmem<DT, FE> smem_views(unsigned char* smem, cons
     S.F = reinterpret_cast<FE*>(smem + L.offF);
     S.Ft = I.symF ? S.F : reinterpret_cast<FE*>(smem + L.offFt);
   }
-  S.P = reinterpret_cast<int8_t*>(smem + L.offP);
-  S.Pt = I.symD ? S.P : reinterpret_cast<int8_t*>(smem + L.offPt);
+  if (STORE & kGlobalP) {
+    S.P = reinterpret_cast<PE*>(ws + p_off);
+    S.Pt = I.symD ? S.P : S.P + (size_t)I.n * I.ldP;
+  } else {
+    S.P = reinterpret_cast<PE*>(smem + L.offP);
+    S.Pt = I.symD ? S.P : reinterpret_cast<PE*>(smem + L.offPt);
+  }
   // workspace: deltas (NT * MAXPT x DT), then tabu stamps (NT * MAXPT x int32)
   S.tabu = (STORE & kGlobalDelta)
                ? reinterpret_cast<int32_t*>(ws + (size_t)NT * MAXPT * sizeof(DT))
@@ -810,7 +871,7 @@ __device__ __forceinline__ void load_instance(const WalkSmem<DT, FE>& S, const I
     int4* sFt = reinterpret_cast<int4*>(S.Ft);
     for (int i = tid; i < nvec; i += NT) sFt[i] = gFt[i];
   }
-  const int pvec = I.n * I.ldP / 16;
+  const int pvec = I.n * I.ldP * (int)sizeof(typename Elem<FE>::P) / 16;
   int4* sP = reinterpret_cast<int4*>(S.P);
   for (int i = tid; i < pvec; i += NT) sP[i] = make_int4(0, 0, 0, 0);
   if (!I.symD) {
@@ -884,9 +945,11 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   __syncthreads();
 
   // P = D[p][p] (and its transpose) gathered from global memory.
+  using PE = typename Elem<FE>::P;
+  const PE* Dg = reinterpret_cast<const PE*>(I.D);
   for (int c = tid; c < n * n; c += NT) {
     const int i = c / n, j = c - (c / n) * n;
-    const int8_t v = I.D[(size_t)S.perm[i] * n + S.perm[j]];
+    const PE v = Dg[(size_t)S.perm[i] * n + S.perm[j]];
     S.P[i * ldP + j] = v;
     if (!I.symD) S.Pt[j * ldP + i] = v;
   }
@@ -1294,7 +1357,7 @@ template <typename DT, typename FE, int NT, int MAXPT, int STORE>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) walk_kernel(const WalkArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* ws = a.ws ? a.ws + a.ws_stride * blockIdx.x : nullptr;
-  const WalkSmem<DT, FE> S = smem_views<DT, FE, NT, MAXPT, STORE>(smem, a.inst, ws);
+  const WalkSmem<DT, FE> S = smem_views<DT, FE, NT, MAXPT, STORE>(smem, a.inst, ws, a.s.p_off);
   const Segment seg = make_segment<MAXPT, interleaved<FE, NT>()>(a.inst.n);
   load_instance<DT, FE, NT, STORE>(S, a.inst);
   for (int w = blockIdx.x; w < a.walks; w += gridDim.x) {
@@ -1325,7 +1388,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) batch_kernel(const BatchAr
     const int inst = b.item_inst[item], w = b.item_walk[item];
     if (inst != cur_inst) {
       I = b.insts[inst];
-      S = smem_views<DT, FE, NT, MAXPT, STORE>(smem, I, ws);
+      S = smem_views<DT, FE, NT, MAXPT, STORE>(smem, I, ws, b.s.p_off);
       seg = make_segment<MAXPT, interleaved<FE, NT>()>(I.n);
       load_instance<DT, FE, NT, STORE>(S, I);
       cur_inst = inst;
@@ -1341,9 +1404,9 @@ using BatchKernelFn = void (*)(const BatchArgs);
 // ---------------------------------------------------------------------------
 // Eq. 1 for a batch of permutations: one CTA per permutation.
 // ---------------------------------------------------------------------------
-template <typename FE, int NT>
+template <typename FE, typename PE, int NT>
 __global__ void __launch_bounds__(NT) cost_kernel(const FE* __restrict__ F, int ldF,
-                                                 const int8_t* __restrict__ D, int n,
+                                                 const PE* __restrict__ D, int n,
                                                  const int32_t* __restrict__ p, int count,
                                                  int64_t* __restrict__ out) {
   __shared__ int64_t red[32];

@@ -9,7 +9,12 @@
 // the arena range for the next request.  The arena is one device allocation
 // made at creation and carved first-fit, so no cudaMalloc or cudaFree (and
 // none of the device-wide synchronisation cudaFree implies) happens while
-// serving.  Every host wait is bounded.
+// serving.  The submitting thread builds each request's upload images and
+// places them in a pinned host slab (also allocated once), so the worker
+// only enqueues copies and launches; pinned output buffers are sized at
+// creation and, if a request ever needs more, replaced without freeing the
+// old ones until the server is destroyed (cudaFreeHost synchronises the
+// device).  Every host wait is bounded.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -81,17 +86,21 @@ struct Request {
   uint64_t ticket = 0;
   DevInstance di;
   int dbytes = 4, fbytes = 2;
-  std::vector<unsigned char> iF, iFt, iD;  // upload images
+  std::vector<unsigned char> iF, iFt, iD;  // upload images (while not in the pinned slab)
+  size_t szF = 0, szFt = 0, szD = 0;       // image sizes
+  size_t host_off = 0, host_bytes = 0;     // range of the images in the pinned slab (bytes 0: none)
   qap_search_params params{};
   // placement on the device
   Plan plan{};
   int grid = 0, smem = 0;
   const void* fn = nullptr;
   size_t off = 0, bytes = 0, offF = 0, offFt = 0, offD = 0, offOut = 0, offWs = 0, ws_stride = 0;
+  size_t p_off = 0, rws_off = 0;  // offsets inside a CTA's workspace slice
   int slot = -1;
   // results (host copies) and times
   std::vector<unsigned char> out;  // the device output block
   Clock::time_point t_submit, t_admit, t_done;
+  double k_start_us = -1, k_end_us = -1;  // device clock of the kernel, from the server's creation
   qap_status result = QAP_OK;
   char err[256] = "";  // CUDA error text recorded by the worker thread
   bool done = false;
@@ -100,10 +109,15 @@ struct Request {
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  unsigned char* pinned = nullptr;  // upload images, then the output block
+  cudaEvent_t k0 = nullptr, k1 = nullptr;  // timing events around the kernel
+  unsigned char* pinned = nullptr;  // upload images (when not in the slab), then the outputs
   size_t pinned_bytes = 0;
   Request* req = nullptr;
 };
+
+// Pinned bytes each slot starts with: the outputs of 64 walks of n = 256,
+// or the images of an int8/int16 instance of n = 256.
+constexpr size_t kSlotPinnedBytes = 512 << 10;
 
 double us_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::micro>(b - a).count();
@@ -116,6 +130,13 @@ struct qap_server {
   qap_server_config cfg{};
   unsigned char* arena_base = nullptr;
   Arena arena;
+  // pinned host slab of upload images, filled by the submitting threads
+  unsigned char* slab = nullptr;
+  Arena slab_arena;
+  std::mutex slab_mu;
+  std::vector<unsigned char*> retired;  // pinned buffers replaced while serving
+  cudaEvent_t ref = nullptr;             // device-clock origin of the kernel times
+  int64_t peak_in_flight = 0;
   std::vector<Slot> slots;
   std::vector<int> free_slots;
   std::mutex mu;
@@ -147,7 +168,10 @@ qap_status place(qap_server* sv, Request* r) {
   QAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->fn, r->plan.nt, r->smem));
   if (occ < 1) return QAP_EUNSUPPORTED;
   r->grid = std::min(W, occ * sv->sms);
-  r->ws_stride = workspace_per_cta(r->plan, r->dbytes, n, &r->params);
+  const WsLayout wl = ws_layout(r->plan, r->dbytes, r->fbytes, n, &r->params);
+  r->ws_stride = wl.stride;
+  r->p_off = wl.p_off;
+  r->rws_off = wl.rws_off;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -163,12 +187,14 @@ qap_status place(qap_server* sv, Request* r) {
   return QAP_OK;
 }
 
-qap_status ensure_pinned(Slot& sl, size_t bytes) {
+// A slot's pinned buffer of at least `bytes`; a smaller one is kept aside
+// (freed at destruction) because cudaFreeHost would synchronise the device.
+qap_status ensure_pinned(qap_server* sv, Slot& sl, size_t bytes) {
   if (sl.pinned_bytes >= bytes) return QAP_OK;
-  if (sl.pinned) cudaFreeHost(sl.pinned);
-  sl.pinned = nullptr;
-  sl.pinned_bytes = 0;
-  QAP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&sl.pinned), bytes, cudaHostAllocDefault));
+  unsigned char* p = nullptr;
+  QAP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&p), bytes, cudaHostAllocDefault));
+  if (sl.pinned) sv->retired.push_back(sl.pinned);
+  sl.pinned = p;
   sl.pinned_bytes = bytes;
   return QAP_OK;
 }
@@ -178,37 +204,52 @@ qap_status launch(qap_server* sv, Request* r) {
   Slot& sl = sv->slots[r->slot];
   const int W = r->params.starts, n = r->di.n;
   const OutLayout OL = out_layout(W, n);
-  const size_t up = r->iF.size() + r->iFt.size() + r->iD.size();
-  QAP_TRY(ensure_pinned(sl, std::max(up, OL.total)));
+  const size_t up = r->host_bytes ? 0 : r->iF.size() + r->iFt.size() + r->iD.size();
+  QAP_TRY(ensure_pinned(sv, sl, std::max(up, OL.total)));
   unsigned char* dev = sv->arena_base + r->off;
-  // stage the images in pinned memory and upload them
-  size_t at = 0;
-  auto stage = [&](const std::vector<unsigned char>& v, size_t dev_off) -> cudaError_t {
-    if (v.empty()) return cudaSuccess;
-    std::memcpy(sl.pinned + at, v.data(), v.size());
-    cudaError_t e =
-        cudaMemcpyAsync(dev + dev_off, sl.pinned + at, v.size(), cudaMemcpyHostToDevice, sl.stream);
-    at += v.size();
-    return e;
-  };
-  // the pinned staging is reused for the outputs only after the uploads ran
-  QAP_CUDA(stage(r->iF, r->offF));
-  if (!r->di.symF) QAP_CUDA(stage(r->iFt, r->offFt));
-  QAP_CUDA(stage(r->iD, r->offD));
+  if (r->host_bytes) {
+    // the images are in the pinned slab already: copies only
+    const unsigned char* h = sv->slab + r->host_off;
+    QAP_CUDA(cudaMemcpyAsync(dev + r->offF, h, r->szF, cudaMemcpyHostToDevice, sl.stream));
+    h += Arena::round(r->szF);
+    if (!r->di.symF) {
+      QAP_CUDA(cudaMemcpyAsync(dev + r->offFt, h, r->szFt, cudaMemcpyHostToDevice, sl.stream));
+      h += Arena::round(r->szFt);
+    }
+    QAP_CUDA(cudaMemcpyAsync(dev + r->offD, h, r->szD, cudaMemcpyHostToDevice, sl.stream));
+  } else {
+    // stage the images in the slot's pinned memory and upload them
+    size_t at = 0;
+    auto stage = [&](const std::vector<unsigned char>& v, size_t dev_off) -> cudaError_t {
+      if (v.empty()) return cudaSuccess;
+      std::memcpy(sl.pinned + at, v.data(), v.size());
+      cudaError_t e = cudaMemcpyAsync(dev + dev_off, sl.pinned + at, v.size(),
+                                      cudaMemcpyHostToDevice, sl.stream);
+      at += v.size();
+      return e;
+    };
+    // the pinned staging is reused for the outputs only after the uploads ran
+    QAP_CUDA(stage(r->iF, r->offF));
+    if (!r->di.symF) QAP_CUDA(stage(r->iFt, r->offFt));
+    QAP_CUDA(stage(r->iD, r->offD));
+  }
   qapk::WalkArgs a{};
   a.inst = inst_args(r->di, dev + r->offF, dev + r->offFt,
-                     reinterpret_cast<const int8_t*>(dev + r->offD), r->plan.nt, r->fbytes);
+                     dev + r->offD, r->plan.nt, r->fbytes);
   const qap_walk_outputs d = carve_outputs(reinterpret_cast<char*>(dev + r->offOut), OL, W);
   a.s = make_search_args(&r->params, &d, n);
-  a.s.rws_off = delta_workspace(r->plan, r->dbytes);
+  a.s.rws_off = r->rws_off;
+  a.s.p_off = r->p_off;
   a.walks = W;
   a.walk_offset = 0;
   a.starts = nullptr;
   a.ws_stride = r->ws_stride;
   a.ws = r->ws_stride ? dev + r->offWs : nullptr;
   const auto fn = reinterpret_cast<qapk::WalkKernelFn>(const_cast<void*>(r->fn));
+  QAP_CUDA(cudaEventRecord(sl.k0, sl.stream));
   fn<<<r->grid, r->plan.nt, r->smem, sl.stream>>>(a);
   QAP_CUDA(cudaGetLastError());
+  QAP_CUDA(cudaEventRecord(sl.k1, sl.stream));
   QAP_CUDA(cudaMemcpyAsync(sl.pinned, dev + r->offOut, OL.total, cudaMemcpyDeviceToHost,
                            sl.stream));
   QAP_CUDA(cudaEventRecord(sl.done, sl.stream));
@@ -221,8 +262,19 @@ void finish(qap_server* sv, int slot_idx, qap_status st) {
   if (st == QAP_OK) {
     const OutLayout OL = out_layout(r->params.starts, r->di.n);
     r->out.assign(sl.pinned, sl.pinned + OL.total);
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, sv->ref, sl.k0) == cudaSuccess &&
+        cudaEventElapsedTime(&b, sv->ref, sl.k1) == cudaSuccess) {
+      r->k_start_us = 1e3 * a;
+      r->k_end_us = 1e3 * b;
+    }
   }
   if (st == QAP_ECUDA) snprintf(r->err, sizeof(r->err), "%s", g_last_error);
+  if (r->host_bytes) {
+    std::lock_guard<std::mutex> hk(sv->slab_mu);
+    sv->slab_arena.release(r->host_off, r->host_bytes);
+    r->host_bytes = 0;
+  }
   std::lock_guard<std::mutex> lk(sv->mu);
   sv->arena.release(r->off, r->bytes);
   r->iF.clear();
@@ -264,6 +316,7 @@ void worker_loop(qap_server* sv) {
       sv->free_slots.pop_back();
       sv->slots[r->slot].req = r;
       ++sv->in_flight;
+      sv->peak_in_flight = std::max(sv->peak_in_flight, sv->in_flight);
       r->t_admit = Clock::now();
       lk.unlock();
       const qap_status st = launch(sv, r);
@@ -308,13 +361,27 @@ qap_status qap_server_create(const qap_server_config* cfg, qap_server** out) {
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&sv->arena_base), (size_t)cfg->mem_bytes);
   if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? QAP_ENOMEM : cuda_fail(e, "cudaMalloc"));
   sv->arena.init((size_t)cfg->mem_bytes);
+  // pinned slab of upload images: a quarter of the device arena, 8 to 256 MiB
+  const size_t slab = std::min<size_t>(256u << 20, std::max<size_t>(8u << 20, cfg->mem_bytes / 4));
+  e = cudaHostAlloc(reinterpret_cast<void**>(&sv->slab), slab, cudaHostAllocDefault);
+  if (e != cudaSuccess) return fail(QAP_ENOMEM);
+  sv->slab_arena.init(slab);
   sv->slots.resize(cfg->slots);
   for (int i = 0; i < cfg->slots; ++i) {
-    e = cudaStreamCreateWithFlags(&sv->slots[i].stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->slots[i].done, cudaEventDisableTiming);
+    Slot& sl = sv->slots[i];
+    e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&sl.k0);
+    if (e == cudaSuccess) e = cudaEventCreate(&sl.k1);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreate"));
+    st = ensure_pinned(sv, sl, kSlotPinnedBytes);
+    if (st != QAP_OK) return fail(st);
     sv->free_slots.push_back(cfg->slots - 1 - i);
   }
+  e = cudaEventCreate(&sv->ref);
+  if (e == cudaSuccess) e = cudaEventRecord(sv->ref, sv->slots[0].stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(sv->ref);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaEventRecord"));
   sv->worker = std::thread(worker_loop, sv);
   *out = sv;
   return QAP_OK;
@@ -330,17 +397,41 @@ qap_status qap_server_submit(qap_server* sv, const int64_t* F, const int64_t* D,
   if (!r) return QAP_ENOMEM;
   QAP_TRY(inspect_instance(F, D, n, &r->di));
   // int64 deltas when B, or B plus the largest frequency penalty, needs them
-  r->dbytes = ((flags & QAP_FORCE_INT64) || r->di.bound > (int64_t)INT_MAX - 1 ||
+  r->dbytes = ((flags & QAP_FORCE_INT64) || r->di.wide || r->di.bound > (int64_t)INT_MAX - 1 ||
                check_penalty(params, 4, r->di.bound) != QAP_OK) ? 8 : 4;
   r->fbytes = flow_bytes(r->di, r->dbytes);
   r->di.ldF = pad_ldF(n, r->fbytes);
-  r->di.ldP = pad_ldP(n);
+  r->di.ldP = pad_ldP(n, pbytes_of(r->fbytes));
   r->params = *params;
   build_images(F, D, r->di, r->fbytes, r->iF, r->iFt, r->iD);
   if (r->di.symF) r->iFt.clear();
-  QAP_CUDA(cudaSetDevice(sv->device));
+  DeviceGuard dg;
+  QAP_TRY(dg.set(sv->device));
   QAP_TRY(place(sv, r.get()));
   if (r->bytes > sv->arena.size()) return QAP_ENOMEM;  // could never be admitted
+  // the images into the pinned slab when it has room, so the worker only
+  // enqueues their copies
+  r->szF = r->iF.size();
+  r->szFt = r->iFt.size();
+  r->szD = r->iD.size();
+  const size_t hb = Arena::round(r->szF) + Arena::round(r->szFt) + Arena::round(r->szD);
+  {
+    std::lock_guard<std::mutex> hk(sv->slab_mu);
+    if (sv->slab_arena.alloc(hb, &r->host_off)) r->host_bytes = hb;
+  }
+  if (r->host_bytes) {
+    unsigned char* h = sv->slab + r->host_off;
+    std::memcpy(h, r->iF.data(), r->szF);
+    h += Arena::round(r->szF);
+    if (r->szFt) {
+      std::memcpy(h, r->iFt.data(), r->szFt);
+      h += Arena::round(r->szFt);
+    }
+    std::memcpy(h, r->iD.data(), r->szD);
+    std::vector<unsigned char>().swap(r->iF);
+    std::vector<unsigned char>().swap(r->iFt);
+    std::vector<unsigned char>().swap(r->iD);
+  }
   r->t_submit = Clock::now();
   std::lock_guard<std::mutex> lk(sv->mu);
   r->ticket = sv->next_ticket++;
@@ -385,6 +476,8 @@ qap_status qap_server_wait(qap_server* sv, uint64_t ticket, int32_t timeout_ms,
     times->queued_us = us_between(r->t_submit, r->t_admit);
     times->device_us = us_between(r->t_admit, r->t_done);
     times->total_us = us_between(r->t_submit, r->t_done);
+    times->kernel_start_us = r->k_start_us;
+    times->kernel_end_us = r->k_end_us;
   }
   sv->all.erase(it);
   return st;
@@ -399,6 +492,7 @@ qap_status qap_server_get_stats(qap_server* sv, qap_server_stats* out) {
   out->in_flight = sv->in_flight;
   out->arena_bytes = (int64_t)sv->arena.size();
   out->arena_used = (int64_t)sv->arena.used();
+  out->peak_in_flight = sv->peak_in_flight;
   return QAP_OK;
 }
 
@@ -412,9 +506,14 @@ void qap_server_destroy(qap_server* sv) {
   for (Slot& sl : sv->slots) {
     if (sl.stream) cudaStreamSynchronize(sl.stream);
     if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.k0) cudaEventDestroy(sl.k0);
+    if (sl.k1) cudaEventDestroy(sl.k1);
     if (sl.stream) cudaStreamDestroy(sl.stream);
     if (sl.pinned) cudaFreeHost(sl.pinned);
   }
+  for (unsigned char* p : sv->retired) cudaFreeHost(p);
+  if (sv->ref) cudaEventDestroy(sv->ref);
+  if (sv->slab) cudaFreeHost(sv->slab);
   if (sv->arena_base) cudaFree(sv->arena_base);
   delete sv;
 }

@@ -72,16 +72,19 @@ void check_choose_plan() {
       }
 }
 
-qaph::DevInstance make_instance(int n, bool symmetric, bool wide_flows, unsigned seed,
-                                int* fbytes, int dbytes) {
+// wide_flows: flows up to 3000 (int16 elements); big_dist: distances up to
+// 30000 (beyond int8: the int64 element path)
+qaph::DevInstance make_instance(int n, bool symmetric, bool wide_flows, bool big_dist,
+                                unsigned seed, int* fbytes, int dbytes) {
   std::mt19937 rng(seed);
   std::vector<int64_t> F((size_t)n * n, 0), D((size_t)n * n, 0);
   const int fmax = wide_flows ? 3000 : 99;
+  const int dmax = big_dist ? 30000 : 99;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
       if (i == j || (symmetric && j < i)) continue;
       F[(size_t)i * n + j] = rng() % (fmax + 1);
-      D[(size_t)i * n + j] = rng() % 100;
+      D[(size_t)i * n + j] = rng() % (dmax + 1);
       if (symmetric) {
         F[(size_t)j * n + i] = F[(size_t)i * n + j];
         D[(size_t)j * n + i] = D[(size_t)i * n + j];
@@ -89,9 +92,10 @@ qaph::DevInstance make_instance(int n, bool symmetric, bool wide_flows, unsigned
     }
   qaph::DevInstance di;
   if (qaph::inspect_instance(F.data(), D.data(), n, &di) != QAP_OK) std::printf("inspect failed\n");
+  if (di.wide != (big_dist ? 1 : 0)) std::printf("FAIL element path of n=%d\n", n), ++fails;
   *fbytes = qaph::flow_bytes(di, dbytes);
   di.ldF = qaph::pad_ldF(n, *fbytes);
-  di.ldP = qaph::pad_ldP(n);
+  di.ldP = qaph::pad_ldP(n, qaph::pbytes_of(*fbytes));
   return di;
 }
 
@@ -100,12 +104,13 @@ qaph::DevInstance make_instance(int n, bool symmetric, bool wide_flows, unsigned
 void check_choose_plan_fit() {
   const int optin = 232448;
   for (int n = 2; n <= 256; n += (n < 40 ? 1 : 3))
-    for (int kind = 0; kind < 6; ++kind) {
-      const bool sym = kind & 1, wide = (kind >> 1) == 1, i64 = (kind >> 1) == 2;
+    for (int kind = 0; kind < 8; ++kind) {
+      const bool sym = kind & 1, wide = (kind >> 1) == 1, i64 = (kind >> 1) >= 2;
+      const bool big = (kind >> 1) == 3;
       const int dbytes = i64 ? 8 : 4;
       int fbytes = 0;
-      const qaph::DevInstance di = make_instance(n, sym, wide, 1000u + n * 7 + kind, &fbytes,
-                                                 dbytes);
+      const qaph::DevInstance di = make_instance(n, sym, wide, big, 1000u + n * 7 + kind,
+                                                 &fbytes, dbytes);
       for (int reserve : {0, 16})
         for (int many = 0; many < 2; ++many) {
           Plan p{};
@@ -116,6 +121,31 @@ void check_choose_plan_fit() {
           }
           const int smem = qaph::plan_smem(p, &di, 1, fbytes, dbytes);
           if (smem + reserve > optin) fail("shared memory exceeded", n, 0, many, p);
+          if (fbytes == 8) {
+            // int64 elements: F always global, P global only where it does
+            // not fit, no products form; the workspace plan only beyond the
+            // register plans
+            if (!(p.store & qapk::kGlobalFlow)) fail("int64 flows not global", n, 0, many, p);
+            if (p.store & qapk::kProductM) fail("products form on int64", n, 0, many, p);
+            if (p.store & qapk::kGlobalP) {
+              Plan q = p;
+              q.store &= ~qapk::kGlobalP;
+              if (qaph::plan_smem(q, &di, 1, fbytes, dbytes) + reserve <= optin)
+                fail("P global where it fits", n, 0, many, p);
+            }
+            if (!fits(n, p)) fail("plan does not hold n", n, 0, many, p);
+            if (p.store & qapk::kGlobalDelta) {
+              if (p.nt != qaph::kLargePlan.nt || p.maxpt != qaph::kLargePlan.maxpt)
+                fail("not the large plan", n, 0, many, p);
+              if (n <= 181) fail("int64 workspace plan within the register plans", n, 0, many, p);
+            } else {
+              if (n > 181) fail("register plan beyond 181", n, 0, many, p);
+              if (!compiled_register_plan(Plan{p.nt, p.maxpt, 0}))
+                fail("not a compiled plan", n, 0, many, p);
+            }
+            continue;
+          }
+          if (p.store & qapk::kGlobalP) fail("P global on a narrow path", n, 0, many, p);
           const int base = p.store & ~qapk::kProductM;
           if (base != 0) {
             // the workspace plan: beyond the register plans' n, or where the
@@ -155,11 +185,36 @@ void check_choose_plan_fit() {
 
 }  // namespace
 
+// The admission of an instance to an element path (no GPU): the narrow
+// path holds every dot-product sum of 2n element products below 2^31, so
+// the int16-flow extremes F = -32768, D = -128 are narrow up to n = 255 and
+// wide at n = 256; the int64 path stops where the bound B reaches 2^62.
+void check_admission() {
+  auto admit = [](int n, int64_t f, int64_t d, qaph::DevInstance* di) {
+    std::vector<int64_t> F((size_t)n * n, f), D((size_t)n * n, d);
+    return qaph::inspect_instance(F.data(), D.data(), n, di);
+  };
+  qaph::DevInstance di;
+  if (admit(255, -32768, -128, &di) != QAP_OK || di.wide) fail("n=255 extremes", 255, 0, 0, {});
+  if (admit(256, -32768, -128, &di) != QAP_OK || !di.wide) fail("n=256 extremes", 256, 0, 0, {});
+  if (admit(20, 32767, 127, &di) != QAP_OK || di.wide || di.bytevec)
+    fail("int16 flows", 20, 0, 0, {});
+  if (admit(20, 99, 128, &di) != QAP_OK || !di.wide) fail("D beyond int8", 20, 0, 0, {});
+  if (admit(20, 32768, 1, &di) != QAP_OK || !di.wide) fail("F beyond int16", 20, 0, 0, {});
+  // B = 52 * 2^40 * 2^19 = 2^64.7: refused; F = 2^40, D = 2^15, n = 2: B = 52 * 2^55 < 2^62
+  if (admit(2, (int64_t)1 << 40, 1 << 19, &di) != QAP_EOVERFLOW) fail("bound", 2, 0, 0, {});
+  if (admit(2, (int64_t)1 << 40, 1 << 15, &di) != QAP_OK || !di.wide)
+    fail("big flows admitted", 2, 0, 0, {});
+  if (admit(3, INT64_MIN, 1, &di) != QAP_EOVERFLOW) fail("INT64_MIN", 3, 0, 0, {});
+  if (admit(257, 0, 0, &di) != QAP_EUNSUPPORTED) fail("n beyond 256", 257, 0, 0, {});
+}
+
 int main() {
   if (qapk::row_segments(256, qaph::kLargePlan.maxpt) > qaph::kLargePlan.nt) {
     std::printf("FAIL the large plan does not hold n = 256\n");
     return 1;
   }
+  check_admission();
   check_choose_plan();
   check_choose_plan_fit();
   if (fails) {

@@ -46,11 +46,17 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
     with pytest.raises(q.QapError) as e:
         q.qap_create(np.zeros((1, 1)), np.zeros((1, 1)))
     assert e.value.status == q.EINVAL
-    big = np.zeros((4, 4), dtype=np.int64)
-    big[0, 1] = 300  # D outside int8
+    # B = (n^2 + 8n + 32) max|F| max|D| = 80 * 2^40 * 2^22 >= 2^62: no exact
+    # int64 path for it
+    F = np.full((4, 4), 1 << 40, dtype=np.int64)
+    D = np.full((4, 4), -(1 << 22), dtype=np.int64)
     with pytest.raises(q.QapError) as e:
-        q.qap_create(np.zeros((4, 4)), big)
-    assert e.value.status == q.EUNSUPPORTED
+        q.qap_create(F, D)
+    assert e.value.status == q.EOVERFLOW
+    F[0, 0] = np.iinfo(np.int64).min  # |F| itself beyond int64
+    with pytest.raises(q.QapError) as e:
+        q.qap_create(F, np.ones((4, 4), dtype=np.int64))
+    assert e.value.status == q.EOVERFLOW
     with pytest.raises(q.QapError) as e:
         q.qap_create(np.zeros((300, 300)), np.zeros((300, 300)))
     assert e.value.status == q.EUNSUPPORTED

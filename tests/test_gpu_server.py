@@ -54,26 +54,44 @@ def test_requests_equal_oracle_and_alone():
             assert times["total_us"] >= times["device_us"] > 0
 
 
+def overlaps(a, b):
+    """Kernel intervals (device clock) of two requests share some time."""
+    return a["kernel_start_us"] < b["kernel_end_us"] and b["kernel_start_us"] < a["kernel_end_us"]
+
+
 def test_result_is_the_same_alone_and_in_the_mix():
     """One request served alone, then the same request among 40 others that
-    were admitted before and after it: identical results."""
+    were admitted before and after it: identical results, and the request's
+    kernel ran on the device at the same time as another request's."""
     probe = instances.poisson_requests(1, seed=7, nmin=60, nmax=60)[0]
     prm = request_params(probe.inst.n, 999, iters=300, walks=16)
     mix = instances.poisson_requests(40, seed=8, nmin=12, nmax=200)
     with q.Server(slots=16, mem_bytes=512 << 20) as sv:
         t0 = sv.submit(probe.inst.F, probe.inst.D, prm)
-        solo, _ = sv.wait(t0)
+        solo, solo_t = sv.wait(t0)
         tickets = []
         for k, r in enumerate(mix):
             tickets.append(sv.submit(r.inst.F, r.inst.D, request_params(r.inst.n, r.rid)))
             if k == 20:
                 t_mid = sv.submit(probe.inst.F, probe.inst.D, prm)
+        in_mix, mid_t = sv.wait(t_mid)
+        others = [sv.wait(t)[1] for t in tickets]
         stats = sv.stats()
-        in_mix, _ = sv.wait(t_mid)
-        for t in tickets:
-            sv.wait(t)
-        assert stats["submitted"] == 42
+    assert stats["submitted"] == 42 and stats["completed"] == 42
     assert same(solo, in_mix)
+    # the device clock orders each request's kernel interval
+    for t in [solo_t, mid_t] + others:
+        assert 0 <= t["kernel_start_us"] < t["kernel_end_us"]
+    assert any(overlaps(mid_t, t) for t in others), "the probe ran alone on the device"
+    assert stats["peak_in_flight"] >= 2
+    # more than one request's kernel at once, at some moment of the mix
+    ev = sorted([(t["kernel_start_us"], 1) for t in others] +
+                [(t["kernel_end_us"], -1) for t in others])
+    depth = peak = 0
+    for _, d in ev:
+        depth += d
+        peak = max(peak, depth)
+    assert peak >= 2
 
 
 def test_admission_by_memory_budget():
@@ -83,15 +101,16 @@ def test_admission_by_memory_budget():
     with q.Server(slots=12, mem_bytes=24 << 20) as sv:
         tickets = [sv.submit(r.inst.F, r.inst.D, request_params(r.inst.n, r.rid, iters=40))
                    for r in reqs]
-        peak = 0
         for _ in range(50):
             st = sv.stats()
-            peak = max(peak, st["in_flight"])
             assert st["arena_used"] <= st["arena_bytes"]
         for r, t in zip(reqs, tickets):
             res, _ = sv.wait(t)
             assert same(res, alone(r.inst.F, r.inst.D, request_params(r.inst.n, r.rid, iters=40)))
-        assert sv.stats()["completed"] == 12
+        st = sv.stats()
+        assert st["completed"] == 12
+        # the arena holds a few of these requests at a time, not all twelve
+        assert 2 <= st["peak_in_flight"] < 12
 
 
 def test_wait_is_bounded_and_tickets_are_checked():
