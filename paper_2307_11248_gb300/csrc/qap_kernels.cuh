@@ -973,9 +973,15 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     compute_g<DT, FE, NT>(S, S.g0, n, ldF, ldP, sym, G);
   DeltaSlots<DT, NT, MAXPT, (STORE & kGlobalDelta) != 0> dl(ws);
   // owner pass form: the O(1) update everywhere, then the rows r and s
-  // apart (register slots), or one pass choosing per slot (workspace slots,
-  // read and written once)
-  constexpr bool kSplitPass = !(STORE & kGlobalDelta);
+  // apart (split), or one pass choosing per slot (fused).  Workspace slots
+  // are read and written once (fused).  Register slots: split up to 8 slots
+  // and with int64 deltas, fused for int32 deltas beyond 8 slots, where the
+  // second pass over the segments of rows r and s, run by a few threads
+  // while the others wait at the barrier, costs more than one select per
+  // slot (n = 100 grid, 256 x 24: 180.8 -> 162.9 ms per step; the int64
+  // batch classes were 6 % slower fused).
+  constexpr bool kSplitPass =
+      !(STORE & kGlobalDelta) && (MAXPT <= 8 || sizeof(DT) == 8);
 #pragma unroll
   for (int i = 0; i < MAXPT; ++i) {
     dl.set(i, i < slen ? delta_serial<DT, FE>(S, n, ldF, ldP, sym, su, sv + i * sk)
