@@ -529,7 +529,7 @@ def measure_batch512(args, q, stream, flush, dev, world, rank, khash, baselines=
     prm = q.make_params(W, seed=w["seed"], iters=iters, tenure=tenure, tenure_per_n=True,
                         walk_base=replica_walk_base(rank, W))
     t0 = time.perf_counter()
-    tune = b.autotune(prm, trial_iters=max(50, iters // 20))
+    tune = [] if args.no_tune else b.autotune(prm, trial_iters=max(50, iters // 20))
     tune_s = time.perf_counter() - t0
     outs = b.device_outputs(W, device=dev)
     step = lambda: b.search_async(prm, outs, stream=stream)  # noqa: E731
@@ -767,6 +767,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--no-nested", action="store_true",
                     help="batch512 only: skip the nested asym50 and grid100 lines")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batch512: the rule's plans, without the autotuner (profiling)")
     ap.add_argument("--threads-per-walk", type=int, default=0)
     ap.add_argument("--iters", type=int, default=0,
                     help="override the iteration count (smaller cases for profiling)")

@@ -21,6 +21,7 @@ namespace qapk {
     case 5121610: return K<DT, FE, 512, 16, kGlobalFlow | kGlobalP>; \
     case 5122010: return K<DT, FE, 512, 20, kGlobalFlow | kGlobalP>; \
     case 5122410: return K<DT, FE, 512, 24, kGlobalFlow | kGlobalP>; \
+    case 5122610: return K<DT, FE, 512, 26, kGlobalFlow | kGlobalP>; \
     case 10240810: return K<DT, FE, 1024, 8, kGlobalFlow | kGlobalP>; \
     case 10241210: return K<DT, FE, 1024, 12, kGlobalFlow | kGlobalP>; \
     case 10241610: return K<DT, FE, 1024, 16, kGlobalFlow | kGlobalP>; \

@@ -76,7 +76,7 @@ inline constexpr Plan kLargePlan = {1024, 40, qapk::kGlobalDelta};
 inline constexpr Plan kPlans[] = {{128, 4, 0},   {128, 12, 0},  {256, 6, 0},   {256, 8, 0},
                        {256, 12, 0},  {256, 16, 0},  {256, 24, 0},
                        {512, 4, 0},   {512, 8, 0},   {512, 12, 0},  {512, 16, 0},
-                       {512, 20, 0},  {512, 24, 0},  {1024, 8, 0},  {1024, 12, 0},
+                       {512, 20, 0},  {512, 24, 0},  {512, 26, 0},  {1024, 8, 0},  {1024, 12, 0},
                        {1024, 16, 0}, {1024, 20, 0}};
 
 inline bool plan_for(int n, int nt, Plan* out) {

@@ -22,6 +22,7 @@ WalkKernelFn walk_kernel_i32_f8m(int nt, int maxpt, int store);  // qap_walk_i32
     case 512160: return K<DT, FE, 512, 16, 0>;                   \
     case 512200: return K<DT, FE, 512, 20, 0>;                   \
     case 512240: return K<DT, FE, 512, 24, 0>;                   \
+    case 512260: return K<DT, FE, 512, 26, 0>;                   \
     case 1024080: return K<DT, FE, 1024, 8, 0>;                  \
     case 1024120: return K<DT, FE, 1024, 12, 0>;                 \
     case 1024160: return K<DT, FE, 1024, 16, 0>;                 \

@@ -24,6 +24,7 @@ WalkKernelFn walk_kernel_i64_f64p(int nt, int maxpt, int store);  // qap_walk_i6
     case 5121602: return K<DT, FE, 512, 16, kGlobalFlow>; \
     case 5122002: return K<DT, FE, 512, 20, kGlobalFlow>; \
     case 5122402: return K<DT, FE, 512, 24, kGlobalFlow>; \
+    case 5122602: return K<DT, FE, 512, 26, kGlobalFlow>; \
     case 10240802: return K<DT, FE, 1024, 8, kGlobalFlow>; \
     case 10241202: return K<DT, FE, 1024, 12, kGlobalFlow>; \
     case 10241602: return K<DT, FE, 1024, 16, kGlobalFlow>; \

@@ -126,3 +126,21 @@ def test_fewer_walks_same_plan_by_request(n, slots):
         assert plan["pairs_per_thread"] == slots, plan
         g = inst.search(prm)
     check_rows(g, F, D, list(range(5)), seed=33, iters=500, tenure=tn)
+
+
+@pytest.mark.parametrize("n,sym,scale,int64", [(150, False, 1, False), (148, True, 1, False),
+                                               (151, False, 90, True), (147, True, 90, True)])
+def test_512x26_plan(n, sym, scale, int64):
+    """n = 147-151 on 512 threads takes 26 slots per thread (the largest batch
+    class's plan, in place of 1024 threads at 64 registers), with int8 or
+    int16 flows and int32 or int64 deltas."""
+    F, D = instances.uniform_instance(n, 990 + n, symmetric=sym)
+    F = F * scale
+    tn = instances.periodic_tenure(n)
+    with q.Instance(F, D, force_int64=int64) as inst:
+        prm = q.make_params(3, seed=34, iters=300, tenure=tn, descend=True,
+                            threads_per_walk=512)
+        plan = inst.plan(prm)
+        assert (plan["threads_per_walk"], plan["pairs_per_thread"]) == (512, 26), plan
+        g = inst.search(prm)
+    check_rows(g, F, D, [0, 1, 2], seed=34, iters=300, tenure=tn, descend=True)
