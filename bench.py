@@ -591,7 +591,11 @@ def measure_batch512(args, q, stream, flush, dev, world, rank, khash, baselines=
     roof["dominant_class"] = class_entry(dom)
     roof["dominant_class"]["note"] = ("the class kernel with the longest launch, timed by CUDA "
                                       "events on the stream it runs on; classes overlap, so "
-                                      "shares add up to more than 1")
+                                      "shares add up to more than 1 and a launch's time "
+                                      "includes waiting for SMs the other classes hold")
+    heavy = int(np.argmax(cls_bytes))
+    roof["heaviest_class"] = class_entry(heavy)
+    roof["heaviest_class"]["note"] = "the class with the most algorithmic bytes per step"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": sum(ms) / args.steps,
         "steps": args.steps, "warmup": args.warmup, "dtype": "int64",
