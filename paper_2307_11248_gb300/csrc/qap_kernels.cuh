@@ -486,14 +486,16 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
     // g-task k = r: Ar with the row s in place of k; k = s: As with row r
     const int kq = gt ? (k == r ? s : r) : k;
     // scalars of the finish; loaded before the dots so their latency hides
-    // under them, except at 1024 threads, whose 64 registers cannot hold them
+    // under them, except at 1024 threads, whose 64 registers cannot hold
+    // them, and with int64 deltas (2.3 % faster on the int64 batch classes
+    // loaded after: fewer live registers across the dot products)
     struct Fin { SC Frk, Fsk, Fkr, Fks, Qrk, Qsk, Qkr, Qks, Fkk, Qkk; DT gck; };
     auto load_fin = [&]() {
       return Fin{F[r * ldF + k],  F[s * ldF + k],  Ft[r * ldF + k], Ft[s * ldF + k],
                  Q[r * ldP + k],  Q[s * ldP + k],  Qt[r * ldP + k], Qt[s * ldP + k],
                  F[k * ldF + k],  Q[k * ldP + k],  gc[k]};
     };
-    constexpr bool kEarly = NT < 1024;
+    constexpr bool kEarly = NT < 1024 && sizeof(DT) == 4;
     Fin fin{};
     if constexpr (kEarly) fin = load_fin();
     const FV* Fk = reinterpret_cast<const FV*>(F + kq * ldF);
@@ -972,16 +974,11 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   else
     compute_g<DT, FE, NT>(S, S.g0, n, ldF, ldP, sym, G);
   DeltaSlots<DT, NT, MAXPT, (STORE & kGlobalDelta) != 0> dl(ws);
-  // owner pass form: the O(1) update everywhere, then the rows r and s
-  // apart (split), or one pass choosing per slot (fused).  Workspace slots
-  // are read and written once (fused).  Register slots: split up to 8 slots
-  // and with int64 deltas, fused for int32 deltas beyond 8 slots, where the
-  // second pass over the segments of rows r and s, run by a few threads
-  // while the others wait at the barrier, costs more than one select per
-  // slot (n = 100 grid, 256 x 24: 180.8 -> 162.9 ms per step; the int64
-  // batch classes were 6 % slower fused).
-  constexpr bool kSplitPass =
-      !(STORE & kGlobalDelta) && (MAXPT <= 8 || sizeof(DT) == 8);
+  // owner pass form: the O(1) update everywhere with the rows r and s
+  // handled inside the pass or after it (split), or one pass choosing per
+  // slot between both values (fused).  Workspace slots are read and written
+  // once (fused); register slots take the split pass (see kInlineRS).
+  constexpr bool kSplitPass = !(STORE & kGlobalDelta);
 #pragma unroll
   for (int i = 0; i < MAXPT; ++i) {
     dl.set(i, i < slen ? delta_serial<DT, FE>(S, n, ldF, ldP, sym, su, sv + i * sk)
@@ -1060,11 +1057,15 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         for (int i = 0; i < MAXPT; ++i)
           if (at_s(i)) nrs = -dl.get(i);
       }
-      // Rows r and s (tu): with int64 deltas their owners take the
-      // recomputed value in this same pass (measured 3.2 % faster on the
-      // int64 batch classes); with int32 deltas they recompute and rescan
-      // their segments after it (3.3 % faster at 6 slots).
-      constexpr bool kInlineRS = sizeof(DT) == 8;
+      // Rows r and s (tu): with int64 deltas or more than 8 slots their
+      // owners take the recomputed value in this same pass, the row read
+      // by those threads only (int64 batch classes 3.2 % faster; n = 100
+      // grid, 256 x 24: 163.1 -> 156.6 ms, where a fused pass loading both
+      // values for every slot had given 162.9 against the 180.8 of a
+      // separate rescan); with int32 deltas and at most 8 slots they
+      // recompute and rescan their segments after it (3.3 % faster at 6
+      // slots than inline).
+      constexpr bool kInlineRS = sizeof(DT) == 8 || MAXPT > 8;
       const int ubase = su == r ? 0 : n;
       const DT gu = su == r ? gr : gs;
 #pragma unroll
