@@ -31,7 +31,7 @@
 //            updated delta enters the scan of the next iteration (tabu /
 //            aspiration filter, lowest (rank, r, s)).  Rows and columns r, s
 //            of P (and P^T) are then exchanged and p[r], p[s] swapped; with
-//            kProductM every thread also brings its share of M up to date.
+//            kProductM every thread then brings its share of M up to date.
 //   -- barrier --  (inside the CTA arg-min: warp REDUX, then one round
 //                   through shared memory)
 // Dot products over all j count the j = x and j = k terms; removing them and
@@ -485,19 +485,6 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
     //         As = F[s].Q[k] + F^T[s].Q^T[k]   Bs = F[k].Q[r] + F^T[k].Q^T[r]
     // g-task k = r: Ar with the row s in place of k; k = s: As with row r
     const int kq = gt ? (k == r ? s : r) : k;
-    // scalars of the finish; loaded before the dots so their latency hides
-    // under them, except at 1024 threads, whose 64 registers cannot hold
-    // them, and with int64 deltas (2.3 % faster on the int64 batch classes
-    // loaded after: fewer live registers across the dot products)
-    struct Fin { SC Frk, Fsk, Fkr, Fks, Qrk, Qsk, Qkr, Qks, Fkk, Qkk; DT gck; };
-    auto load_fin = [&]() {
-      return Fin{F[r * ldF + k],  F[s * ldF + k],  Ft[r * ldF + k], Ft[s * ldF + k],
-                 Q[r * ldP + k],  Q[s * ldP + k],  Qt[r * ldP + k], Qt[s * ldP + k],
-                 F[k * ldF + k],  Q[k * ldP + k],  gc[k]};
-    };
-    constexpr bool kEarly = NT < 1024 && sizeof(DT) == 4;
-    Fin fin{};
-    if constexpr (kEarly) fin = load_fin();
     const FV* Fk = reinterpret_cast<const FV*>(F + kq * ldF);
     const FV* Ftk = reinterpret_cast<const FV*>(Ft + kq * ldF);
     const QV* Qk = reinterpret_cast<const QV*>(Q + kq * ldP);
@@ -549,12 +536,16 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
       gn[k] = sym ? (DT)2 * ((DT)A0 + (DT)c1) : (DT)A0 + (DT)c1 + (DT)c2;
       continue;
     }
-    if constexpr (!kEarly) fin = load_fin();
-    const SC Frk = fin.Frk, Fsk = fin.Fsk, Fkr = fin.Fkr, Fks = fin.Fks;
-    const SC Qrk = fin.Qrk, Qsk = fin.Qsk, Qkr = fin.Qkr, Qks = fin.Qks;
-    const SC Fkk = fin.Fkk, Qkk = fin.Qkk;
+    // scalars of the finish, loaded after the dot products: held across
+    // them they cost registers (measured: int64 batch classes 2.3 %, the
+    // n = 100 grid 1.7 % faster loaded here)
+    const SC Frk = F[r * ldF + k], Fsk = F[s * ldF + k];
+    const SC Fkr = Ft[r * ldF + k], Fks = Ft[s * ldF + k];
+    const SC Qrk = Q[r * ldP + k], Qsk = Q[s * ldP + k];
+    const SC Qkr = Qt[r * ldP + k], Qks = Qt[s * ldP + k];
+    const SC Fkk = F[k * ldF + k], Qkk = Q[k * ldP + k];
     const SC a = Frk - Fsk, b = Qrk - Qsk, c = Fkr - Fks, e = Qkr - Qks;
-    const DT gk = fin.gck - (DT)(a * b) - (DT)(c * e);
+    const DT gk = gc[k] - (DT)(a * b) - (DT)(c * e);
     for (int xi = lg; xi < 2; xi += (G == 1 ? 1 : 2)) {
       const bool xs = xi != 0;
       const SC fxx = xs ? fSS : fRR;   // F[x][x]
@@ -677,7 +668,7 @@ __device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, int8_t>& S, cons
 // (r s): with P'[i][j] = P[t(i)][t(j)], the row-x terms change only at
 // j in {r, s}.  A thread keeps one group of 4 consecutive columns (16-byte
 // loads and stores) and walks down the rows; in the group holding column r
-// or s, those columns take the other column's entry and word.  Runs beside
+// or s, those columns take the other column's entry and word.  Runs after
 // the owner pass, which does not read M; the next iteration reads Mn after
 // its arg-min barrier.  Columns past n are padding.
 template <int NT>
@@ -1018,7 +1009,6 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     const typename VO::U uu = VO::prep(vec[su]);
     const DT gr = gn[r], gs = gn[s];
     const bool tu = (su == r) | (su == s);        // every pair of the segment touches
-    const DT xr = S.R[su] - gr, xs = S.R[n + su] - gs;
     // admissible: not tabu (mark <= nit), or aspiring (ncur + d < nbest,
     // i.e. d < nbest - ncur, clamped where no delta can reach it)
     const int tlim = tabu ? nit : INT_MAX;
@@ -1035,7 +1025,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     };
     bd = DeltaMax<DT>::v;
     bk = kNoMove;
-    int irs = -1;  // interleaved: slot of the pair (r, s), where held
+    [[maybe_unused]] int irs = -1;  // interleaved: slot of the pair (r, s), where held
     // interleaved: the slots' v are recomputed in each pass rather than held
     // across the iterations (which costs MAXPT registers)
     int sv = seg_sv, sk = seg_sk;
@@ -1050,6 +1040,8 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       else return i == is;
     };
     if constexpr (kSplitPass) {
+      // new deltas of the pairs (su, r) and (su, s) of other rows
+      const DT xr = S.R[su] - gr, xs = S.R[n + su] - gs;
       // the pair (r, s) itself only changes sign
       DT nrs = 0;
       if (su == r) {
@@ -1191,14 +1183,17 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       if (warp0) dh = fnv_step(dh, r, s);
       phase_x_any(r, s);
       __syncthreads();
+      update_and_scan(std::false_type{}, r, s, false, 0, 0, cur, cur, bd, bk);
+      swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
       if constexpr ((STORE & kProductM) != 0) {
+        // M after the move (Mn read by the next phase X, after the next
+        // arg-min's barrier); after the owner pass, so that each thread's
+        // candidate is ready first (asym50 10.14 -> 10.04 ms per step)
         phase_m_update<NT>(Mc, Mn, vw, n, r, s);
         int32_t* t = Mc;
         Mc = Mn;
         Mn = t;
       }
-      update_and_scan(std::false_type{}, r, s, false, 0, 0, cur, cur, bd, bk);
-      swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
       DT* t = gc; gc = gn; gn = t;
     }
     __syncthreads();
@@ -1286,12 +1281,6 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       }
       phase_x_any(r, s);
       __syncthreads();
-      if constexpr ((STORE & kProductM) != 0) {
-        phase_m_update<NT>(Mc, Mn, vw, n, r, s);
-        int32_t* t = Mc;
-        Mc = Mn;
-        Mn = t;
-      }
       int stamp = it + tenure;
       const bool owner =
           su == r && (kInterleave ? slot_of(s) >= 0 : s >= sv && s < sv + slen);
@@ -1341,6 +1330,15 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       update_and_scan(ext, r, s, true, it + 1, stamp, cur, best, bd, bk);
       if (fq && owner) atomicAdd(fq + s * a.p_stride + r, 1);
       swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
+      if constexpr ((STORE & kProductM) != 0) {
+        // M after the move (Mn read by the next phase X, after the next
+        // arg-min's barrier); after the owner pass, so that each thread's
+        // candidate is ready first (asym50 10.14 -> 10.04 ms per step)
+        phase_m_update<NT>(Mc, Mn, vw, n, r, s);
+        int32_t* t = Mc;
+        Mc = Mn;
+        Mn = t;
+      }
       DT* t = gc; gc = gn; gn = t;
     }
   };
