@@ -122,8 +122,9 @@ constexpr int kGlobalDelta = 1;
 constexpr int kGlobalFlow = 2;
 // Plans with bit kProductM (int8 flows) keep the n x n products
 //   M[x][k] = sum_j F[x][j] P[k][j] + F[j][x] P[j][k]
-// in shared memory and update them after each move (see phase_m_update),
-// so that phase X reads the dot products it needs instead of computing them.
+// in shared memory, their columns indexed by unit (see compute_m), and
+// update them after each move (see phase_m_update), so that phase X reads
+// the dot products it needs instead of computing them.
 constexpr int kProductM = 4;
 // Plans with bit kGlobalP (int64 elements only) keep P and P^T in the CTA's
 // workspace (at SearchArgs::p_off) instead of shared memory; they read F and
@@ -172,7 +173,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int ldF, int fbytes, in
   L.offRedK = o; o = align16(o + 32 * 4);
   L.offSum = o;  o = align16(o + 32 * 8);
   // M twice (current and next) and the update words of the indices
-  L.offM = o;    o = (store & kProductM) ? align16(o + 2 * n * ld_m(n) * 4 + ld_m(n) * 4) : o;
+  L.offM = o;    o = (store & kProductM) ? align16(o + (n + 2) * ld_m(n) * 4) : o;
   L.bytes = o;
   return L;
 }
@@ -267,6 +268,28 @@ template <> struct VecOps<int8_t> {
     // wrap-around sums: only the final value is bounded
     return (DT)((uint32_t)d + (uint32_t)u.w + (uint32_t)v.y - (uint32_t)__dp4a(u.A, v.x, 0));
   }
+  __device__ __forceinline__ static void put(void* vec, int, int k, V v) {
+    reinterpret_cast<V*>(vec)[k] = v;
+  }
+  __device__ __forceinline__ static V get(const void* vec, int, int k) {
+    return reinterpret_cast<const V*>(vec)[k];
+  }
+};
+
+// int8 flows, the word alone: index x stores only the bytes (b, e, a, c),
+// and each reader recomputes w_x with one dp4a against (a, c, 0, 0).  Each
+// slot then loads 4 bytes instead of 8 (shorter per-thread strides, fewer
+// bank conflicts) at two more instructions.  Measured faster on the
+// 6-slot products plan only (n = 50 asymmetric, 256 walks: 10.05 -> 9.82 ms
+// per step); 0.2-2 % slower on the other int8 plans measured.
+struct VecOpsWord : VecOps<int8_t> {
+  __device__ __forceinline__ static void put(void* vec, int, int k, V v) {
+    reinterpret_cast<int*>(vec)[k] = v.x;
+  }
+  __device__ __forceinline__ static V get(const void* vec, int, int k) {
+    const int x = reinterpret_cast<const int*>(vec)[k];
+    return make_int2(x, __dp4a(x, (int)__byte_perm((uint32_t)x, 0u, 0x4432u), 0));
+  }
 };
 
 template <> struct VecOps<int16_t> {
@@ -279,6 +302,12 @@ template <> struct VecOps<int16_t> {
   template <typename DT>
   __device__ __forceinline__ static DT update(const U& u, const V v, DT d) {
     return d + (DT)((u.x - v.x) * (u.y - v.y) + (u.z - v.z) * (u.w - v.w));
+  }
+  __device__ __forceinline__ static void put(void* vec, int, int k, V v) {
+    reinterpret_cast<V*>(vec)[k] = v;
+  }
+  __device__ __forceinline__ static V get(const void* vec, int, int k) {
+    return reinterpret_cast<const V*>(vec)[k];
   }
 };
 
@@ -297,6 +326,12 @@ template <> struct VecOps<int64_t> {
   template <typename DT>
   __device__ __forceinline__ static DT update(const U& u, const V v, DT d) {
     return d + (DT)((u.a - v.a) * (u.b - v.b) + (u.c - v.c) * (u.e - v.e));
+  }
+  __device__ __forceinline__ static void put(void* vec, int, int k, V v) {
+    reinterpret_cast<V*>(vec)[k] = v;
+  }
+  __device__ __forceinline__ static V get(const void* vec, int, int k) {
+    return reinterpret_cast<const V*>(vec)[k];
   }
 };
 
@@ -372,7 +407,7 @@ struct WalkSmem {
   DT* redD;
   uint32_t* redK;
   int64_t* sum;
-  int32_t* M;  // kProductM plans: two n x ld_m(n) buffers, then ld_m(n) words
+  int32_t* M;  // kProductM plans: M (n x ld_m(n)), then two rows of ld_m(n) update words
 };
 
 // Eq. 2 (with the diagonal term) for the pair {x, k}, by one thread, from the
@@ -568,7 +603,7 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
       S.R[xi * n + k] = cross + (DT)sig - gk + (DT)corr;
     }
     if (lg == 0) {
-      reinterpret_cast<typename VO::V*>(S.vec)[k] = VO::pack(a, b, c, e);
+      VO::put(S.vec, n, k, VO::pack(a, b, c, e));
       gn[k] = gk;
     }
   }
@@ -577,10 +612,19 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
 // ---------------------------------------------------------------------------
 // Phase X from maintained products (plans with kProductM, int8 flows)
 // ---------------------------------------------------------------------------
-// M from the current P into buffer Mc, at the start of a walk: one dot
-// product per entry (two when F or D is asymmetric).  M[k][k] is g[k].
+// The products are kept with their columns indexed by unit rather than by
+// location: Mt[x][p[k]] = M[x][k] = F[x].Q[k] + F^T[x].Q^T[k], p the current
+// permutation.  A move (r s) changes Q only at the rows and columns r, s, and
+// a unit's column does not move with it: every entry takes the same rank-2
+// update
+//   Mt'[x][f] = Mt[x][f] - a_x b_j - c_x e_j,   j the location of unit f
+// before the move (with a, b, c, e the update vector of phase X), in place
+// and with no exchange of columns.
+
+// Mt from the current P and p, at the start of a walk: one dot product per
+// entry (two when F or D is asymmetric).  Mt[k][p[k]] is g[k].
 template <int NT>
-__device__ __forceinline__ void compute_m(const WalkSmem<int32_t, int8_t>& S, int32_t* Mc, int n,
+__device__ __forceinline__ void compute_m(const WalkSmem<int32_t, int8_t>& S, int32_t* Mt, int n,
                                           int ldF, int ldP, bool sym) {
   using C = Chunk<int8_t>;
   const int nc = (n + C::W - 1) / C::W, ldm = ld_m(n);
@@ -595,43 +639,46 @@ __device__ __forceinline__ void compute_m(const WalkSmem<int32_t, int8_t>& S, in
       acc = C::dot(Fx[c], Pk[c], acc);
       if (!sym) acc = C::dot(Ftx[c], Ptk[c], acc);
     }
-    Mc[x * ldm + k] = sym ? 2 * acc : acc;
+    Mt[x * ldm + S.perm[k]] = sym ? 2 * acc : acc;
   }
 }
 
-// Phase X of move (r, s) from M (pre-move, buffer Mc): one thread per index
-// k writes the update vector of k (also as one word in vw, for
-// phase_m_update) and, for k outside {r, s}, the recomputed deltas of the
-// pairs {r, k} and {s, k}, whose dot products are the entries
+// Phase X of move (r, s) from Mt (pre-move): one thread per index k writes
+// the update vector of k, also as one word by index (vw[k], whose bytes a_k,
+// c_k phase_m_update reads per row) and by unit (vwu[p[k]], its b_k, e_k per
+// column), and, for k outside {r, s}, the recomputed deltas of the pairs
+// {r, k} and {s, k}, whose dot products are the entries
 //   F[r].Q[k] + F^T[r].Q^T[k] = M[r][k],  F[k].Q[s] + F^T[k].Q^T[s] = M[k][s]
 // (and the same with r, s exchanged); the threads of k = r and k = s write
-// g'[r] = M'[r][r] and g'[s] = M'[s][s] (see phase_m_update).  The finish
-// is the one of phase_x.
-template <typename DT, int NT>
-__device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, int8_t>& S, const int32_t* M,
-                                             int32_t* vw, DT* gn, int n, int ldF, int ldP, int r,
-                                             int s) {
-  using VO = VecOps<int8_t>;
+// g'[r] = M'[r][r] = M[r][s] - a_r b_s - c_r e_s and g'[s] likewise.  The
+// finish is the one of phase_x.
+template <typename DT, int NT, typename VO>
+__device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, int8_t>& S, const int32_t* Mt,
+                                             int32_t* vw, int32_t* vwu, DT* gn, int n, int ldF,
+                                             int ldP, int r, int s) {
   const int8_t* F = S.F;
   const int8_t* Ft = S.Ft;
   const int8_t* Q = S.P;
   const int8_t* Qt = S.Pt;
   const int ldm = ld_m(n);
+  const int pr = S.perm[r], ps = S.perm[s];
   for (int k = threadIdx.x; k < n; k += NT) {
+    const int pk = S.perm[k];
     const int Frk = F[r * ldF + k], Fsk = F[s * ldF + k];
     const int Fkr = Ft[r * ldF + k], Fks = Ft[s * ldF + k];
     const int Qrk = Q[r * ldP + k], Qsk = Q[s * ldP + k];
     const int Qkr = Qt[r * ldP + k], Qks = Qt[s * ldP + k];
     const int a = Frk - Fsk, b = Qrk - Qsk, c = Fkr - Fks, e = Qkr - Qks;
     const typename VO::V v = VO::pack(a, b, c, e);
-    reinterpret_cast<typename VO::V*>(S.vec)[k] = v;
+    VO::put(S.vec, n, k, v);
     vw[k] = v.x;
+    vwu[pk] = v.x;
     if (k == r || k == s) {
       // g'[x] = M[x][xb] - c_x e_xb - a_x b_xb, xb the other of r, s
       const int xb = k == s ? r : s;
       const int exb = Qt[r * ldP + xb] - Qt[s * ldP + xb];
       const int bxb = Q[r * ldP + xb] - Q[s * ldP + xb];
-      gn[k] = (DT)M[k * ldm + xb] - (DT)(c * exb) - (DT)(a * bxb);
+      gn[k] = (DT)Mt[k * ldm + (k == s ? pr : ps)] - (DT)(c * exb) - (DT)(a * bxb);
       continue;
     }
     const int fRR = F[r * ldF + r], fRS = F[r * ldF + s];
@@ -639,7 +686,7 @@ __device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, int8_t>& S, cons
     const int qRR = Q[r * ldP + r], qRS = Q[r * ldP + s];
     const int qSR = Q[s * ldP + r], qSS = Q[s * ldP + s];
     const int Fkk = F[k * ldF + k], Qkk = Q[k * ldP + k];
-    const DT gk = (DT)M[k * ldm + k] - (DT)(a * b) - (DT)(c * e);
+    const DT gk = (DT)Mt[k * ldm + pk] - (DT)(a * b) - (DT)(c * e);
 #pragma unroll
     for (int xi = 0; xi < 2; ++xi) {
       const bool xs = xi != 0;
@@ -655,57 +702,46 @@ __device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, int8_t>& S, cons
       const int qsr_xb = xs ? qSR - qRR : qSS - qRS;
       const int corr = (fxx - fxk - fkx + Fkk) * (pxx - pxk - pkx + Qkk);
       const int sig = -fx_rs * e - frs_x * b + qxb_sr * c + qsr_xb * a;
-      const int Ax = M[(xs ? s : r) * ldm + k];
-      const int Bx = M[k * ldm + (xs ? r : s)];
+      const int Ax = Mt[(xs ? s : r) * ldm + pk];  // M[x][k]
+      const int Bx = Mt[k * ldm + (xs ? pr : ps)];  // M[k][xb]
       S.R[xi * n + k] = (DT)Ax + (DT)Bx + (DT)sig - gk + (DT)corr;
     }
   }
 }
 
-// M after move (r, s), from Mc into Mn, with the update words vw of
-// phase_m_prep:
-//   M'[x][k] = M[x][t(k)] - a_x b_t(k) - c_x e_t(k),  t the transposition
-// (r s): with P'[i][j] = P[t(i)][t(j)], the row-x terms change only at
-// j in {r, s}.  A thread keeps one group of 4 consecutive columns (16-byte
-// loads and stores) and walks down the rows; in the group holding column r
-// or s, those columns take the other column's entry and word.  Runs after
-// the owner pass, which does not read M; the next iteration reads Mn after
-// its arg-min barrier.  Columns past n are padding.
-template <int NT>
-__device__ __forceinline__ void phase_m_update(const int32_t* Mc, int32_t* Mn, const int32_t* vw,
-                                               int n, int r, int s) {
-  const int ldm = ld_m(n), gpr = ldm / 4;
-  const int rows = NT / gpr;  // rows per pass: every thread below rows * gpr has a group
-  const int g = threadIdx.x % gpr, x0 = threadIdx.x / gpr;
-  if (x0 >= rows) return;
-  const int k0 = 4 * g;
-  int4 w = reinterpret_cast<const int4*>(vw)[g];
-  const int jr = r - k0, js = s - k0;  // positions of columns r, s in this group
-  const bool hr = (unsigned)jr < 4u, hs = (unsigned)js < 4u;
-  if (hr | hs) {
-    const int wr = vw[r], ws = vw[s];
-    if (jr == 0 || js == 0) w.x = jr == 0 ? ws : wr;
-    if (jr == 1 || js == 1) w.y = jr == 1 ? ws : wr;
-    if (jr == 2 || js == 2) w.z = jr == 2 ? ws : wr;
-    if (jr == 3 || js == 3) w.w = jr == 3 ? ws : wr;
-  }
-  for (int x = x0; x < n; x += rows) {
-    // bytes (a_x, c_x, 0, 0) against (b, e, a, c) of each column
+// A thread's share of the Mt update: one group of 4 consecutive unit columns
+// (16-byte loads and stores) on every rows-th row from x0.  Fixed per walk.
+struct MShare {
+  int g, x0, rows;
+};
+
+__device__ __forceinline__ MShare m_share(int n, int nt) {
+  const int gpr = ld_m(n) / 4;  // groups per row
+  const int rows = nt / gpr;     // rows per pass: every thread below rows * gpr has a group
+  return MShare{(int)threadIdx.x % gpr, (int)threadIdx.x / gpr, rows};
+}
+
+// Mt after move (r, s), in place, with the update words of phase_m_prep:
+//   Mt'[x][f] -= (a_x, c_x) . (b_j, e_j),  j the location of unit f before
+// the move, as one dp4a of the bytes (a_x, c_x, 0, 0) of vw[x] with vwu[f]
+// = (b_j, e_j, a_j, c_j).  Runs after the owner pass, which does not read
+// Mt; phase_m_prep of this move read it before the barrier that precedes
+// the owner pass, and the next one reads it after the next arg-min's
+// barrier.  Columns past n are padding.
+__device__ __forceinline__ void phase_m_update(int32_t* Mt, const int32_t* vw,
+                                               const int32_t* vwu, int n, MShare sh) {
+  if (sh.x0 >= sh.rows) return;
+  const int ldm = ld_m(n);
+  const int4 w = reinterpret_cast<const int4*>(vwu)[sh.g];
+  for (int x = sh.x0; x < n; x += sh.rows) {
     const int ux = (int)__byte_perm((uint32_t)vw[x], 0u, 0x4432u);
-    const int32_t* Mx = Mc + x * ldm;
-    int4 m = reinterpret_cast<const int4*>(Mx)[g];
-    if (hr | hs) {
-      const int mr = Mx[r], ms = Mx[s];
-      if (jr == 0 || js == 0) m.x = jr == 0 ? ms : mr;
-      if (jr == 1 || js == 1) m.y = jr == 1 ? ms : mr;
-      if (jr == 2 || js == 2) m.z = jr == 2 ? ms : mr;
-      if (jr == 3 || js == 3) m.w = jr == 3 ? ms : mr;
-    }
+    int4* Mx = reinterpret_cast<int4*>(Mt + x * ldm) + sh.g;
+    int4 m = *Mx;
     m.x -= __dp4a(ux, w.x, 0);
     m.y -= __dp4a(ux, w.y, 0);
     m.z -= __dp4a(ux, w.z, 0);
     m.w -= __dp4a(ux, w.w, 0);
-    reinterpret_cast<int4*>(Mn + x * ldm)[g] = m;
+    *Mx = m;
   }
 }
 
@@ -907,6 +943,9 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   const bool sym = I.symF && I.symD;
   const bool warp0 = tid < 32;
   constexpr bool kInterleave = interleaved<FE, NT>();
+  // per-index vectors: the word-only form on the 6-slot products plan
+  using VOsel = std::conditional_t<sizeof(FE) == 1 && (STORE & kProductM) != 0 && MAXPT == 6,
+                                   VecOpsWord, VecOps<FE>>;
   const int su = seg.su, sv = seg.sv, slen = seg.slen, wlen = seg.wlen;
   const int sk = kInterleave ? seg.sk : 1;
   const int seg_sv = sv, seg_sk = sk;
@@ -956,12 +995,15 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     c0 += (int64_t)S.F[i * ldF + j] * (int64_t)S.P[i * ldP + j];
   }
   c0 = block_sum<NT>(c0, S.sum);
-  // maintained products: current and next buffers, and the update words
-  int32_t* Mc = S.M;
-  int32_t* Mn = S.M ? S.M + n * ld_m(n) : nullptr;
-  int32_t* const vw = S.M ? S.M + 2 * n * ld_m(n) : nullptr;
+  // maintained products (columns by unit), the update words by index and
+  // by unit, and this thread's share of the update (held across the walk,
+  // except at 1024 threads, whose 64 registers spill it)
+  int32_t* const Mt = S.M;
+  int32_t* const vw = S.M ? S.M + n * ld_m(n) : nullptr;
+  int32_t* const vwu = S.M ? vw + ld_m(n) : nullptr;
+  [[maybe_unused]] const MShare msh = NT < 1024 ? m_share(n, NT) : MShare{};
   if constexpr ((STORE & kProductM) != 0)
-    compute_m<NT>(S, Mc, n, ldF, ldP, sym);
+    compute_m<NT>(S, Mt, n, ldF, ldP, sym);
   else
     compute_g<DT, FE, NT>(S, S.g0, n, ldF, ldP, sym, G);
   DeltaSlots<DT, NT, MAXPT, (STORE & kGlobalDelta) != 0> dl(ws);
@@ -1004,9 +1046,9 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
                              DT nbest, DT& bd, uint32_t& bk) {
     constexpr bool EXT = decltype(ext)::value;
     const int32_t* crow = EXT ? applied() + su * n : nullptr;
-    using VO = VecOps<FE>;
-    const auto* vec = reinterpret_cast<const typename VO::V*>(S.vec);
-    const typename VO::U uu = VO::prep(vec[su]);
+    using VO = VOsel;
+    const void* vec = S.vec;
+    const typename VO::U uu = VO::prep(VO::get(vec, n, su));
     const DT gr = gn[r], gs = gn[s];
     const bool tu = (su == r) | (su == s);        // every pair of the segment touches
     // admissible: not tabu (mark <= nit), or aspiring (ncur + d < nbest,
@@ -1066,7 +1108,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         const bool valid = i < slen;
         const int vi = sv + i * sk;
         const int v = valid ? vi : sv;
-        DT d = VO::update(uu, vec[v], dl.get(i));
+        DT d = VO::update(uu, VO::get(vec, n, v), dl.get(i));
         d = at_r(i) ? xr : at_s(i) ? xs : d;
         bool isrs = false;
         if constexpr (kInlineRS) {
@@ -1129,7 +1171,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         const int tbl = S.tabu[i * NT + tid];
         const DT gx = tu ? gu : (tvr ? gr : gs);
         DT d = dl.get(i);
-        const DT o1 = VO::update(uu, vec[v], d);
+        const DT o1 = VO::update(uu, VO::get(vec, n, v), d);
         const bool isrs = (su == r) & at_s(i);
         d = isrs ? -d : (tu | tv) ? rv - gx : o1;
         dl.set(i, d);
@@ -1155,7 +1197,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   // by dot products over the rows of F and P.
   auto phase_x_any = [&](int r, int s) {
     if constexpr ((STORE & kProductM) != 0)
-      phase_m_prep<DT, NT>(S, Mc, vw, gn, n, ldF, ldP, r, s);
+      phase_m_prep<DT, NT, VOsel>(S, Mt, vw, vwu, gn, n, ldF, ldP, r, s);
     else
       phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
   };
@@ -1186,13 +1228,10 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       update_and_scan(std::false_type{}, r, s, false, 0, 0, cur, cur, bd, bk);
       swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
       if constexpr ((STORE & kProductM) != 0) {
-        // M after the move (Mn read by the next phase X, after the next
+        // Mt after the move (read by the next phase X, after the next
         // arg-min's barrier); after the owner pass, so that each thread's
         // candidate is ready first (asym50 10.14 -> 10.04 ms per step)
-        phase_m_update<NT>(Mc, Mn, vw, n, r, s);
-        int32_t* t = Mc;
-        Mc = Mn;
-        Mn = t;
+        phase_m_update(Mt, vw, vwu, n, NT < 1024 ? msh : m_share(n, NT));
       }
       DT* t = gc; gc = gn; gn = t;
     }
@@ -1331,13 +1370,10 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       if (fq && owner) atomicAdd(fq + s * a.p_stride + r, 1);
       swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
       if constexpr ((STORE & kProductM) != 0) {
-        // M after the move (Mn read by the next phase X, after the next
+        // Mt after the move (read by the next phase X, after the next
         // arg-min's barrier); after the owner pass, so that each thread's
         // candidate is ready first (asym50 10.14 -> 10.04 ms per step)
-        phase_m_update<NT>(Mc, Mn, vw, n, r, s);
-        int32_t* t = Mc;
-        Mc = Mn;
-        Mn = t;
+        phase_m_update(Mt, vw, vwu, n, NT < 1024 ? msh : m_share(n, NT));
       }
       DT* t = gc; gc = gn; gn = t;
     }
