@@ -112,6 +112,20 @@ typedef struct {
 #define QAP_TABU_UNIT_LOC 1
 #define QAP_TABU_UNIT 2
 
+/* How phase X (Section 4.4: the deltas of the pairs touching the move,
+ * recomputed by Eq. 2) gets its dot products (qap_search_params.phase_x):
+ *   QAP_PHASE_X_AUTO  the n x n products M[x][k] = F[x].P[k] + F^T[x].P^T[k]
+ *                     kept in shared memory and brought up to date by a
+ *                     rank-2 update per move, where they apply: int8 flow
+ *                     storage, int32 deltas, plans of at most 16 pairs per
+ *                     thread (12 at 1024 threads), and an M that fits shared
+ *                     memory (and still lets two walks share an SM where the
+ *                     plan was taken for that); elsewhere dot products;
+ *   QAP_PHASE_X_DOTS  dot products over the rows of F and P at every move.
+ * Both give the same walks; qap_plan reports which one runs. */
+#define QAP_PHASE_X_AUTO 0
+#define QAP_PHASE_X_DOTS 1
+
 typedef struct {
   int32_t n;
   int32_t delta_bytes;     /* 4 (int32 path) or 8 (int64 path)              */
@@ -197,6 +211,7 @@ typedef struct {
                               qap_batch_search_noalloc: QAP_EUNSUPPORTED).
                               The serving loop picks int64 deltas itself
                               when the penalty needs them.                   */
+  int32_t phase_x;         /* QAP_PHASE_X_AUTO (default) or _DOTS          */
 } qap_search_params;
 
 /* Per-walk outputs; every pointer may be NULL except best_cost.  For

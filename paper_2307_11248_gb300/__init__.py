@@ -14,4 +14,5 @@ from ._binding import (  # noqa: F401
     qap_best_walks, qap_batch_set_timing, qap_batch_classes,
     qap_batch_search_noalloc, Server, qap_server_create, qap_server_destroy,
     qap_server_get_stats, qap_server_submit, qap_server_wait, TABU_PAIR, TABU_UNIT_LOC, TABU_UNIT,
+    PHASE_X_AUTO, PHASE_X_DOTS,
 )

@@ -18,6 +18,7 @@ OK, EINVAL, EOVERFLOW, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(7)
 FORCE_INT64 = 1
 LAUNCH_PERSISTENT, LAUNCH_PLAIN = 0, 1
 TABU_PAIR, TABU_UNIT_LOC, TABU_UNIT = 0, 1, 2
+PHASE_X_AUTO, PHASE_X_DOTS = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -49,7 +50,8 @@ class SearchParams(ctypes.Structure):
                 ("iters", ctypes.c_int32), ("tenure", Tenure), ("aspiration", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("launch", ctypes.c_int32),
                 ("threads_per_walk", ctypes.c_int32), ("tenure_per_n", ctypes.c_int32),
-                ("criterion", ctypes.c_int32), ("freq_penalty", ctypes.c_int32)]
+                ("criterion", ctypes.c_int32), ("freq_penalty", ctypes.c_int32),
+                ("phase_x", ctypes.c_int32)]
 
 
 class WalkOutputs(ctypes.Structure):
@@ -203,16 +205,18 @@ def _ptr(a):
 
 def make_params(starts, *, seed=0, iters=0, tenure=(1, 1, 0), aspiration=True, descend=False,
                 max_descent=-1, walk_base=0, launch=LAUNCH_PERSISTENT, threads_per_walk=0,
-                tenure_per_n=False, criterion=0, freq_penalty=0):
+                tenure_per_n=False, criterion=0, freq_penalty=0, phase_x=PHASE_X_AUTO):
     """Search parameters.  With tenure_per_n, `tenure` is given in hundredths
     of each instance's n (e.g. (90, 110, 200) is [0.9n, 1.1n] redrawn every
     2n; (10, 33, 0) is the paper's [0.1n, 0.33n] drawn per move).
     ``criterion`` is TABU_PAIR, TABU_UNIT_LOC or TABU_UNIT; ``freq_penalty``
-    the frequency-based diversification weight (0 = off)."""
+    the frequency-based diversification weight (0 = off); ``phase_x`` is
+    PHASE_X_AUTO (maintained products where they apply) or PHASE_X_DOTS."""
     return SearchParams(int(starts), int(walk_base), int(bool(descend)), int(max_descent),
                         int(iters), Tenure(*[int(t) for t in tenure]), int(bool(aspiration)),
                         int(seed) & (2**64 - 1), int(launch), int(threads_per_walk),
-                        int(bool(tenure_per_n)), int(criterion), int(freq_penalty))
+                        int(bool(tenure_per_n)), int(criterion), int(freq_penalty),
+                        int(phase_x))
 
 
 # ---------------------------------------------------------------------------

@@ -106,7 +106,7 @@ qap_status occupancy(Launch* L, int sms, int work) {
 qap_status plan_ctx(qap_ctx* ctx, const qap_search_params* p, Launch* L) {
   const bool many = p->starts >= 2 * ctx->sms;
   if (!choose_plan_fit(ctx->di.n, p->threads_per_walk, many, &ctx->di, 1, ctx->fbytes,
-                       ctx->dbytes, ctx->smem_optin, 0, &L->plan))
+                       ctx->dbytes, ctx->smem_optin, 0, p->phase_x, &L->plan))
     return QAP_EUNSUPPORTED;
   L->fn = reinterpret_cast<const void*>(pick_walk_kernel(ctx->dbytes, ctx->fbytes, L->plan));
   if (!L->fn) return QAP_EUNSUPPORTED;
@@ -119,7 +119,7 @@ qap_status plan_batch(qap_batch* b, const qap_search_params* p, Launch* L) {
   // the batch kernel also holds one static int
   const bool many = (int64_t)b->count * p->starts >= 2 * (int64_t)b->sms;
   if (!choose_plan_fit(b->nmax, p->threads_per_walk, many, b->di.data(), b->count, b->fbytes,
-                       b->dbytes, b->smem_optin, 16, &L->plan))
+                       b->dbytes, b->smem_optin, 16, p->phase_x, &L->plan))
     return QAP_EUNSUPPORTED;
   L->fn = reinterpret_cast<const void*>(pick_batch_kernel(b->dbytes, b->fbytes, L->plan));
   if (!L->fn) return QAP_EUNSUPPORTED;
@@ -197,13 +197,14 @@ qap_status plan_classes(qap_batch* b, const qap_search_params* p) {
   for (int i = 0; i < b->count; ++i) {
     if (p->threads_per_walk == 0 && !b->tuned.empty() && b->tuned[i].nt != 0) {
       plan_of[i] = b->tuned[i];
+      if (p->phase_x == QAP_PHASE_X_DOTS) plan_of[i].store &= ~qapk::kProductM;
       continue;
     }
     // the batch kernel also holds one static int
     // the classes run together: walks of the whole batch fill the SMs
     const bool many = (int64_t)b->count * W >= 2 * (int64_t)b->sms;
     if (!choose_plan_fit(b->di[i].n, p->threads_per_walk, many, &b->di[i], 1, b->fbytes,
-                         b->dbytes, b->smem_optin, 16, &plan_of[i]))
+                         b->dbytes, b->smem_optin, 16, p->phase_x, &plan_of[i]))
       return QAP_EUNSUPPORTED;
   }
   std::vector<int> order(b->count);
@@ -765,7 +766,8 @@ qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
         cands.push_back(p);
         Plan m = p;
         m.store |= qapk::kProductM;
-        if (b->fbytes == 1 && b->dbytes == 4 && has_product_form(p) && fits(m))
+        if (tp.phase_x != QAP_PHASE_X_DOTS && b->fbytes == 1 && b->dbytes == 4 &&
+            has_product_form(p) && fits(m))
           cands.push_back(m);
       }
     }

@@ -251,17 +251,17 @@ inline bool has_product_form(const Plan& p) {
   return p.store == 0 && (p.nt == 1024 ? p.maxpt <= 12 : p.maxpt <= 16);
 }
 
-// The products form of a register plan when the flows are int8, an
-// instance is asymmetric and M fits shared memory too (phase X then reads M
-// instead of computing dot products).  Measured: asym50 11.3 -> 10.5 ms per
-// step; on symmetric instances, whose dot products are half as many, it
-// gains nothing (grid100 2000 iterations: 46.0 vs 45.8 ms).
+// The products form of a register plan when the flows are int8 and M fits
+// shared memory too (phase X then reads M instead of computing dot
+// products), unless the caller asks for the dot products.  Measured with
+// 2 walks per SM, 4000 iterations: asymmetric n = 60 / 70 / 80 8.4 / 10.4 /
+// 12.9 ms against 10.3 / 11.0 / 13.4 for symmetric ones by dot products;
+// symmetric n = 50 / 60 / 70 / 80 by products 6.7 / 8.4 / 10.3 / 12.7 ms;
+// n = 100 at 512 x 12 symmetric 10.2 against 12.1 ms.  At 24 slots (not
+// compiled with M) the n = 100 grid took 157.8 against 154.2 ms.
 inline Plan with_products(Plan p, const DevInstance* d, int count, int fbytes, int dbytes,
-                          int smem_optin, int reserve) {
-  if (fbytes != 1 || dbytes != 4 || !has_product_form(p)) return p;
-  bool asym = false;
-  for (int i = 0; i < count; ++i) asym |= !(d[i].symF && d[i].symD);
-  if (!asym) return p;
+                          int smem_optin, int reserve, int form) {
+  if (form == QAP_PHASE_X_DOTS || fbytes != 1 || dbytes != 4 || !has_product_form(p)) return p;
   Plan m = p;
   m.store |= qapk::kProductM;
   return plan_smem(m, d, count, fbytes, dbytes) + reserve <= smem_optin ? m : p;
@@ -285,12 +285,13 @@ inline Plan wide_store(Plan p, const DevInstance* d, int count, int fbytes, int 
 // taken for that alone must let two CTAs share an SM (without the products
 // form if need be), else the choice is made as without `many`.
 inline bool choose_plan_fit(int nmax, int threads, bool many, const DevInstance* d, int count,
-                            int fbytes, int dbytes, int smem_optin, int reserve, Plan* out) {
+                            int fbytes, int dbytes, int smem_optin, int reserve, int form,
+                            Plan* out) {
   Plan p;
   if (nmax <= 181 && choose_plan(nmax, threads, many, &p)) {
     p = wide_store(p, d, count, fbytes, dbytes, smem_optin, reserve);
     if (plan_smem(p, d, count, fbytes, dbytes) + reserve <= smem_optin) {
-      Plan m = with_products(p, d, count, fbytes, dbytes, smem_optin, reserve);
+      Plan m = with_products(p, d, count, fbytes, dbytes, smem_optin, reserve, form);
       if (many && threads == 0 && p.nt == 256 && p.maxpt > 8) {
         // two CTAs per SM: each with its own 1 KB reserved by the hardware
         auto two = [&](const Plan& x) {
@@ -300,7 +301,7 @@ inline bool choose_plan_fit(int nmax, int threads, bool many, const DevInstance*
         if (!two(m)) m = p;
         if (!two(m))
           return choose_plan_fit(nmax, threads, false, d, count, fbytes, dbytes, smem_optin,
-                                 reserve, out);
+                                 reserve, form, out);
       }
       *out = m;
       return true;
@@ -445,6 +446,7 @@ inline qap_status validate_params(const qap_search_params* p) {
     return QAP_EINVAL;
   const int t = p->threads_per_walk;
   if (t != 0 && t != 128 && t != 256 && t != 512 && t != 1024) return QAP_EINVAL;
+  if (p->phase_x != QAP_PHASE_X_AUTO && p->phase_x != QAP_PHASE_X_DOTS) return QAP_EINVAL;
   return QAP_OK;
 }
 

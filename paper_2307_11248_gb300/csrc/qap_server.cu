@@ -158,7 +158,7 @@ qap_status place(qap_server* sv, Request* r) {
   // a request's own walks decide (several requests share the GPU)
   const bool many = W >= 2 * sv->sms;
   if (!choose_plan_fit(n, r->params.threads_per_walk, many, &r->di, 1, r->fbytes, r->dbytes,
-                       sv->smem_optin, 0, &r->plan))
+                       sv->smem_optin, 0, r->params.phase_x, &r->plan))
     return QAP_EUNSUPPORTED;
   r->fn = reinterpret_cast<const void*>(pick_walk_kernel(r->dbytes, r->fbytes, r->plan));
   if (!r->fn) return QAP_EUNSUPPORTED;

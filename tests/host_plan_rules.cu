@@ -112,10 +112,11 @@ void check_choose_plan_fit() {
       const qaph::DevInstance di = make_instance(n, sym, wide, big, 1000u + n * 7 + kind,
                                                  &fbytes, dbytes);
       for (int reserve : {0, 16})
+        for (int form : {QAP_PHASE_X_AUTO, QAP_PHASE_X_DOTS})
         for (int many = 0; many < 2; ++many) {
           Plan p{};
           if (!qaph::choose_plan_fit(n, 0, many != 0, &di, 1, fbytes, dbytes, optin, reserve,
-                                     &p)) {
+                                     form, &p)) {
             fail("no plan fits", n, 0, many, p);
             continue;
           }
@@ -170,9 +171,19 @@ void check_choose_plan_fit() {
           if (!compiled_register_plan(reg)) fail("not a compiled plan", n, 0, many, p);
           if (!fits(n, p)) fail("plan does not hold n", n, 0, many, p);
           if (p.store & qapk::kProductM) {
-            if (fbytes != 1 || dbytes != 4 || (di.symF && di.symD))
+            if (fbytes != 1 || dbytes != 4 || form == QAP_PHASE_X_DOTS)
               fail("products form where it does not apply", n, 0, many, p);
             if (!qaph::has_product_form(reg)) fail("products form not compiled", n, 0, many, p);
+          } else if (form == QAP_PHASE_X_AUTO && fbytes == 1 && dbytes == 4 &&
+                     qaph::has_product_form(reg)) {
+            // left out only where M does not fit, or keeps two walks from
+            // sharing an SM where the plan was taken for that
+            Plan m = reg;
+            m.store |= qapk::kProductM;
+            const int ms = qaph::plan_smem(m, &di, 1, fbytes, dbytes);
+            const bool two = many && p.nt == 256 && p.maxpt > 8;
+            if (ms + reserve <= optin && (!two || 2 * (ms + reserve + 1024) <= optin + 1024))
+              fail("products form left out where it fits", n, 0, many, p);
           }
           if (p.nt == 256 && p.maxpt > 8) {
             if (!many) fail("256 wide without walks", n, 0, many, p);

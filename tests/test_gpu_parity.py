@@ -266,7 +266,7 @@ def test_invalid_parameters_are_rejected():
     F, D = rand_instance(13, 10)
     with q.Instance(F, D) as inst:
         for kw in [dict(iters=10, tenure=(0, 3, 0)), dict(iters=10, tenure=(5, 3, 0)),
-                   dict(iters=-1)]:
+                   dict(iters=-1), dict(phase_x=2), dict(phase_x=-1)]:
             with pytest.raises(q.QapError) as e:
                 inst.search(q.make_params(2, seed=1, **kw))
             assert e.value.status == q.EINVAL
@@ -318,14 +318,16 @@ def test_async_search_in_cuda_graph(gpu):
     assert np.array_equal(first["hash"].cpu().numpy().view(np.uint64), o["hash"])
 
 
-@pytest.mark.parametrize("n,sym,products", [(2, False, 1), (3, False, 1), (5, False, 1),
-                                            (17, False, 1), (50, False, 1), (100, False, 1),
-                                            (50, True, 0), (170, False, 0)])
-def test_phase_x_forms_bit_exact(n, sym, products):
-    """Phase X from maintained products (int8 flows, asymmetric, when M fits
-    shared memory) and by dot products (the rest): both equal the oracle."""
+@pytest.mark.parametrize("n,sym,form,products", [
+    (2, False, 0, 1), (3, False, 0, 1), (5, False, 0, 1), (17, False, 0, 1), (50, False, 0, 1),
+    (100, False, 0, 1), (50, True, 0, 1), (100, True, 0, 1), (170, False, 0, 0),
+    (5, False, 1, 0), (50, False, 1, 0), (50, True, 1, 0), (100, False, 1, 0)])
+def test_phase_x_forms_bit_exact(n, sym, form, products):
+    """Phase X from maintained products (int8 flows, when M fits shared
+    memory: the automatic form) and by dot products (asked for, or where the
+    products do not apply): both equal the oracle."""
     F, D = instances.uniform_instance(n, 420 + n, symmetric=sym)
-    prm = q.make_params(4, seed=13, iters=200, tenure=(3, 9, 0), descend=True)
+    prm = q.make_params(4, seed=13, iters=200, tenure=(3, 9, 0), descend=True, phase_x=form)
     with q.Instance(F, D) as inst:
         assert inst.plan(prm)["products"] == products
         g = inst.search(prm)

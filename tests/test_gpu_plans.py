@@ -69,26 +69,27 @@ def test_grid100_full_launch_on_its_own_plan():
         assert np.array_equal(inst.cost(g["best_p"]), g["best_cost"])
 
 
-# (n, symmetric, expected slots, expected products form): every int8 plan with
-# 256 threads that a many-walk launch selects, symmetric instances (the
-# dot-product form of phase X) and asymmetric ones (the products form where
-# it is compiled, up to 16 slots; the dot-product form at 24)
-PLANS_256 = [(50, False, 6, 1), (52, True, 6, 0),
-             (58, False, 8, 1), (60, True, 8, 0),
-             (70, False, 12, 1), (66, True, 12, 0),
-             (80, False, 16, 1), (78, True, 16, 0),
-             (96, False, 24, 0), (90, True, 24, 0)]
+# (n, symmetric, expected slots): every int8 plan with 256 threads that a
+# many-walk launch selects, on symmetric and asymmetric instances, each with
+# phase X from the maintained products (the automatic form where it is
+# compiled, up to 16 slots) and by dot products (asked for, and the
+# automatic form at 24 slots)
+PLANS_256 = [(50, False, 6), (52, True, 6), (58, False, 8), (60, True, 8),
+             (70, False, 12), (66, True, 12), (80, False, 16), (78, True, 16),
+             (96, False, 24), (90, True, 24)]
 
 
-@pytest.mark.parametrize("n,sym,slots,products", PLANS_256)
-def test_many_walk_plans_int8(n, sym, slots, products):
+@pytest.mark.parametrize("phase_x", [q.PHASE_X_AUTO, q.PHASE_X_DOTS])
+@pytest.mark.parametrize("n,sym,slots", PLANS_256)
+def test_many_walk_plans_int8(n, sym, slots, phase_x):
     W = 2 * sms()
     F, D = instances.uniform_instance(n, 600 + n, symmetric=sym)
     tn = instances.periodic_tenure(n)
     iters = 400
+    products = int(phase_x == q.PHASE_X_AUTO and slots <= 16)
     with q.Instance(F, D) as inst:
         assert inst.info["delta_bytes"] == 4
-        prm = q.make_params(W, seed=31, iters=iters, tenure=tn, descend=True)
+        prm = q.make_params(W, seed=31, iters=iters, tenure=tn, descend=True, phase_x=phase_x)
         plan = inst.plan(prm)
         assert plan["threads_per_walk"] == 256 and plan["pairs_per_thread"] == slots, plan
         assert plan["products"] == products and plan["ctas_per_sm"] >= 2, plan
