@@ -172,8 +172,8 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int ldF, int fbytes, in
   L.offRedD = o; o = align16(o + 32 * 8);
   L.offRedK = o; o = align16(o + 32 * 4);
   L.offSum = o;  o = align16(o + 32 * 8);
-  // M twice (current and next) and the update words of the indices
-  L.offM = o;    o = (store & kProductM) ? align16(o + (n + 2) * ld_m(n) * 4) : o;
+  // M, the update words by index and by unit, and sigma (see compute_m)
+  L.offM = o;    o = (store & kProductM) ? align16(o + ((n + 2) * ld_m(n) + n) * 4) : o;
   L.bytes = o;
   return L;
 }
@@ -407,7 +407,7 @@ struct WalkSmem {
   DT* redD;
   uint32_t* redK;
   int64_t* sum;
-  int32_t* M;  // kProductM plans: M (n x ld_m(n)), then two rows of ld_m(n) update words
+  int32_t* M;  // kProductM plans: M (n x ld_m(n)), two rows of ld_m(n) update words, sigma (n)
 };
 
 // Eq. 2 (with the diagonal term) for the pair {x, k}, by one thread, from the
@@ -612,17 +612,21 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
 // ---------------------------------------------------------------------------
 // Phase X from maintained products (plans with kProductM, int8 flows)
 // ---------------------------------------------------------------------------
-// The products are kept with their columns indexed by unit rather than by
-// location: Mt[x][p[k]] = M[x][k] = F[x].Q[k] + F^T[x].Q^T[k], p the current
-// permutation.  A move (r s) changes Q only at the rows and columns r, s, and
-// a unit's column does not move with it: every entry takes the same rank-2
+// These plans neither exchange rows and columns of P nor index M by
+// location.  P keeps the walk's starting matrix P0 = D[p0][p0], and
+// sigma[k] is the row of P0 that location k now holds (p = p0 o sigma), so
+// Q[i][j] = P0[sigma[i]][sigma[j]]; a move (r s) exchanges sigma[r] and
+// sigma[s] only.  The products are kept with their columns indexed by that
+// label rather than by location: Mt[x][sigma[k]] = M[x][k] = F[x].Q[k] +
+// F^T[x].Q^T[k].  A move changes Q only at the rows and columns r, s, and a
+// label's column does not move with it: every entry takes the same rank-2
 // update
-//   Mt'[x][f] = Mt[x][f] - a_x b_j - c_x e_j,   j the location of unit f
+//   Mt'[x][u] = Mt[x][u] - a_x b_j - c_x e_j,   j the location of label u
 // before the move (with a, b, c, e the update vector of phase X), in place
 // and with no exchange of columns.
 
-// Mt from the current P and p, at the start of a walk: one dot product per
-// entry (two when F or D is asymmetric).  Mt[k][p[k]] is g[k].
+// Mt from P0 at the start of a walk (sigma the identity): one dot product
+// per entry (two when F or D is asymmetric).  Mt[k][k] is g[k].
 template <int NT>
 __device__ __forceinline__ void compute_m(const WalkSmem<int32_t, int8_t>& S, int32_t* Mt, int n,
                                           int ldF, int ldP, bool sym) {
@@ -639,54 +643,58 @@ __device__ __forceinline__ void compute_m(const WalkSmem<int32_t, int8_t>& S, in
       acc = C::dot(Fx[c], Pk[c], acc);
       if (!sym) acc = C::dot(Ftx[c], Ptk[c], acc);
     }
-    Mt[x * ldm + S.perm[k]] = sym ? 2 * acc : acc;
+    Mt[x * ldm + k] = sym ? 2 * acc : acc;
   }
 }
 
 // Phase X of move (r, s) from Mt (pre-move): one thread per index k writes
 // the update vector of k, also as one word by index (vw[k], whose bytes a_k,
-// c_k phase_m_update reads per row) and by unit (vwu[p[k]], its b_k, e_k per
-// column), and, for k outside {r, s}, the recomputed deltas of the pairs
-// {r, k} and {s, k}, whose dot products are the entries
+// c_k phase_m_update reads per row) and by label (vwu[sigma[k]], its b_k,
+// e_k per column), and, for k outside {r, s}, the recomputed deltas of the
+// pairs {r, k} and {s, k}, whose dot products are the entries
 //   F[r].Q[k] + F^T[r].Q^T[k] = M[r][k],  F[k].Q[s] + F^T[k].Q^T[s] = M[k][s]
 // (and the same with r, s exchanged); the threads of k = r and k = s write
-// g'[r] = M'[r][r] = M[r][s] - a_r b_s - c_r e_s and g'[s] likewise.  The
-// finish is the one of phase_x.
+// g'[r] = M'[r][r] = M[r][s] - a_r b_s - c_r e_s and g'[s] likewise.  Q is
+// read from P0 through sigma.  The finish is the one of phase_x.
 template <typename DT, int NT, typename VO>
 __device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, int8_t>& S, const int32_t* Mt,
-                                             int32_t* vw, int32_t* vwu, DT* gn, int n, int ldF,
-                                             int ldP, int r, int s) {
+                                             int32_t* vw, int32_t* vwu, const int32_t* sigma,
+                                             DT* gn, int n, int ldF, int ldP, int r, int s) {
   const int8_t* F = S.F;
   const int8_t* Ft = S.Ft;
-  const int8_t* Q = S.P;
-  const int8_t* Qt = S.Pt;
+  const int8_t* P0 = S.P;
+  const int8_t* P0t = S.Pt;
   const int ldm = ld_m(n);
-  const int pr = S.perm[r], ps = S.perm[s];
+  const int ur = sigma[r], us = sigma[s];  // P0 rows of locations r and s
+  const int8_t* Qr = P0 + ur * ldP;         // Q[r][j] = Qr[sigma[j]]
+  const int8_t* Qs = P0 + us * ldP;
+  const int8_t* Qtr = P0t + ur * ldP;       // Q^T[r][j] = Qtr[sigma[j]]
+  const int8_t* Qts = P0t + us * ldP;
   for (int k = threadIdx.x; k < n; k += NT) {
-    const int pk = S.perm[k];
+    const int uk = sigma[k];
     const int Frk = F[r * ldF + k], Fsk = F[s * ldF + k];
     const int Fkr = Ft[r * ldF + k], Fks = Ft[s * ldF + k];
-    const int Qrk = Q[r * ldP + k], Qsk = Q[s * ldP + k];
-    const int Qkr = Qt[r * ldP + k], Qks = Qt[s * ldP + k];
+    const int Qrk = Qr[uk], Qsk = Qs[uk];
+    const int Qkr = Qtr[uk], Qks = Qts[uk];
     const int a = Frk - Fsk, b = Qrk - Qsk, c = Fkr - Fks, e = Qkr - Qks;
     const typename VO::V v = VO::pack(a, b, c, e);
     VO::put(S.vec, n, k, v);
     vw[k] = v.x;
-    vwu[pk] = v.x;
+    vwu[uk] = v.x;
     if (k == r || k == s) {
       // g'[x] = M[x][xb] - c_x e_xb - a_x b_xb, xb the other of r, s
-      const int xb = k == s ? r : s;
-      const int exb = Qt[r * ldP + xb] - Qt[s * ldP + xb];
-      const int bxb = Q[r * ldP + xb] - Q[s * ldP + xb];
-      gn[k] = (DT)Mt[k * ldm + (k == s ? pr : ps)] - (DT)(c * exb) - (DT)(a * bxb);
+      const int uxb = k == s ? ur : us;
+      const int exb = Qtr[uxb] - Qts[uxb];
+      const int bxb = Qr[uxb] - Qs[uxb];
+      gn[k] = (DT)Mt[k * ldm + uxb] - (DT)(c * exb) - (DT)(a * bxb);
       continue;
     }
     const int fRR = F[r * ldF + r], fRS = F[r * ldF + s];
     const int fSR = F[s * ldF + r], fSS = F[s * ldF + s];
-    const int qRR = Q[r * ldP + r], qRS = Q[r * ldP + s];
-    const int qSR = Q[s * ldP + r], qSS = Q[s * ldP + s];
-    const int Fkk = F[k * ldF + k], Qkk = Q[k * ldP + k];
-    const DT gk = (DT)Mt[k * ldm + pk] - (DT)(a * b) - (DT)(c * e);
+    const int qRR = Qr[ur], qRS = Qr[us];
+    const int qSR = Qs[ur], qSS = Qs[us];
+    const int Fkk = F[k * ldF + k], Qkk = P0[uk * ldP + uk];
+    const DT gk = (DT)Mt[k * ldm + uk] - (DT)(a * b) - (DT)(c * e);
 #pragma unroll
     for (int xi = 0; xi < 2; ++xi) {
       const bool xs = xi != 0;
@@ -702,8 +710,8 @@ __device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, int8_t>& S, cons
       const int qsr_xb = xs ? qSR - qRR : qSS - qRS;
       const int corr = (fxx - fxk - fkx + Fkk) * (pxx - pxk - pkx + Qkk);
       const int sig = -fx_rs * e - frs_x * b + qxb_sr * c + qsr_xb * a;
-      const int Ax = Mt[(xs ? s : r) * ldm + pk];  // M[x][k]
-      const int Bx = Mt[k * ldm + (xs ? pr : ps)];  // M[k][xb]
+      const int Ax = Mt[(xs ? s : r) * ldm + uk];  // M[x][k]
+      const int Bx = Mt[k * ldm + (xs ? ur : us)];  // M[k][xb]
       S.R[xi * n + k] = (DT)Ax + (DT)Bx + (DT)sig - gk + (DT)corr;
     }
   }
@@ -1001,9 +1009,12 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   int32_t* const Mt = S.M;
   int32_t* const vw = S.M ? S.M + n * ld_m(n) : nullptr;
   int32_t* const vwu = S.M ? vw + ld_m(n) : nullptr;
+  int32_t* const sigma = S.M ? vwu + ld_m(n) : nullptr;
   [[maybe_unused]] const MShare msh = NT < 1024 ? m_share(n, NT) : MShare{};
-  if constexpr ((STORE & kProductM) != 0)
+  if constexpr ((STORE & kProductM) != 0) {
+    for (int x = tid; x < n; x += NT) sigma[x] = x;
     compute_m<NT>(S, Mt, n, ldF, ldP, sym);
+  }
   else
     compute_g<DT, FE, NT>(S, S.g0, n, ldF, ldP, sym, G);
   DeltaSlots<DT, NT, MAXPT, (STORE & kGlobalDelta) != 0> dl(ws);
@@ -1193,11 +1204,29 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     }
   };
 
+  // The move's exchange: rows and columns r, s of P (and P^T) and p[r],
+  // p[s]; with the maintained products p[r], p[s] and sigma[r], sigma[s]
+  // only (P stays P0).
+  auto apply_move = [&](int r, int s) {
+    if constexpr ((STORE & kProductM) != 0) {
+      if (tid == 0) {
+        int32_t t = S.perm[r];
+        S.perm[r] = S.perm[s];
+        S.perm[s] = t;
+        t = sigma[r];
+        sigma[r] = sigma[s];
+        sigma[s] = t;
+      }
+    } else {
+      swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
+    }
+  };
+
   // Phase X of move (r, s): from the maintained products (kProductM), or
   // by dot products over the rows of F and P.
   auto phase_x_any = [&](int r, int s) {
     if constexpr ((STORE & kProductM) != 0)
-      phase_m_prep<DT, NT, VOsel>(S, Mt, vw, vwu, gn, n, ldF, ldP, r, s);
+      phase_m_prep<DT, NT, VOsel>(S, Mt, vw, vwu, sigma, gn, n, ldF, ldP, r, s);
     else
       phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
   };
@@ -1226,7 +1255,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       phase_x_any(r, s);
       __syncthreads();
       update_and_scan(std::false_type{}, r, s, false, 0, 0, cur, cur, bd, bk);
-      swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
+      apply_move(r, s);
       if constexpr ((STORE & kProductM) != 0) {
         // Mt after the move (read by the next phase X, after the next
         // arg-min's barrier); after the owner pass, so that each thread's
@@ -1368,7 +1397,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
       }
       update_and_scan(ext, r, s, true, it + 1, stamp, cur, best, bd, bk);
       if (fq && owner) atomicAdd(fq + s * a.p_stride + r, 1);
-      swap_rs<NT>(S.P, S.Pt, S.perm, n, ldP, I.symD, r, s);
+      apply_move(r, s);
       if constexpr ((STORE & kProductM) != 0) {
         // Mt after the move (read by the next phase X, after the next
         // arg-min's barrier); after the owner pass, so that each thread's
