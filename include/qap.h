@@ -117,7 +117,7 @@ typedef struct {
  *   QAP_PHASE_X_AUTO  the n x n products M[x][k] = F[x].P[k] + F^T[x].P^T[k]
  *                     kept in shared memory and brought up to date by a
  *                     rank-2 update per move, where they apply: int8 flow
- *                     storage, int32 deltas, plans of at most 16 pairs per
+ *                     storage, int32 deltas, plans of at most 24 pairs per
  *                     thread (12 at 1024 threads), and an M that fits shared
  *                     memory (and still lets two walks share an SM where the
  *                     plan was taken for that); elsewhere dot products;

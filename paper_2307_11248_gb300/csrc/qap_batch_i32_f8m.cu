@@ -13,10 +13,13 @@ namespace qapk {
     case 256084: return K<DT, FE, 256, 8, kProductM>;            \
     case 256124: return K<DT, FE, 256, 12, kProductM>;           \
     case 256164: return K<DT, FE, 256, 16, kProductM>;           \
+    case 256244: return K<DT, FE, 256, 24, kProductM>;           \
     case 512044: return K<DT, FE, 512, 4, kProductM>;            \
     case 512084: return K<DT, FE, 512, 8, kProductM>;            \
     case 512124: return K<DT, FE, 512, 12, kProductM>;           \
     case 512164: return K<DT, FE, 512, 16, kProductM>;           \
+    case 512204: return K<DT, FE, 512, 20, kProductM>;           \
+    case 512244: return K<DT, FE, 512, 24, kProductM>;           \
     case 1024084: return K<DT, FE, 1024, 8, kProductM>;          \
     case 1024124: return K<DT, FE, 1024, 12, kProductM>;         \
     default: return nullptr;                                     \

@@ -246,9 +246,13 @@ inline int plan_smem(const Plan& p, const DevInstance* d, int count, int fbytes,
   return smem;
 }
 
-// Register plans compiled with the maintained products M (int8 flows).
+// Register plans compiled with the maintained products M (int8 flows): up
+// to 24 slots (12 at 1024 threads).  Measured against the dot products at
+// 24 slots: the n = 100 grid 153.5 -> 150.9 ms per step, asymmetric n = 96
+// (2 walks per SM) 14.2 -> 12.8 ms, n = 135 at 512 x 24 15.0 -> 13.2 ms; at
+// 26 slots symmetric n = 148 was slower (14.0 -> 14.3 ms) and is left out.
 inline bool has_product_form(const Plan& p) {
-  return p.store == 0 && (p.nt == 1024 ? p.maxpt <= 12 : p.maxpt <= 16);
+  return p.store == 0 && (p.nt == 1024 ? p.maxpt <= 12 : p.maxpt <= 24);
 }
 
 // The products form of a register plan when the flows are int8 and M fits

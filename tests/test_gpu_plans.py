@@ -49,8 +49,8 @@ def check_rows(g, F, D, rows, **kw):
 def test_grid100_full_launch_on_its_own_plan():
     """The whole n = 100 grid workload in the launch its benchmark times
     (1024 walks, 2opt to a local minimum, then 10^4 tabu iterations): the
-    automatic plan is 256 threads x 24 slots, two CTAs per SM; sampled walks
-    equal the oracle's."""
+    automatic plan is 256 threads x 24 slots, two CTAs per SM, with phase X
+    from the maintained products; sampled walks equal the oracle's."""
     w = instances.workload_grid100()
     W = w["walks"]
     assert W >= 2 * sms()
@@ -59,7 +59,7 @@ def test_grid100_full_launch_on_its_own_plan():
                             descend=True)
         plan = inst.plan(prm)
         assert (plan["threads_per_walk"], plan["pairs_per_thread"]) == (256, 24), plan
-        assert plan["ctas_per_sm"] == 2 and plan["products"] == 0, plan
+        assert plan["ctas_per_sm"] == 2 and plan["products"] == 1, plan
         g = inst.search(prm)
     assert (g["iters_done"] == w["iters"]).all()
     check_rows(g, w["F"], w["D"], [0, 1, 511, 700, 1022, 1023], seed=w["seed"],
@@ -71,9 +71,8 @@ def test_grid100_full_launch_on_its_own_plan():
 
 # (n, symmetric, expected slots): every int8 plan with 256 threads that a
 # many-walk launch selects, on symmetric and asymmetric instances, each with
-# phase X from the maintained products (the automatic form where it is
-# compiled, up to 16 slots) and by dot products (asked for, and the
-# automatic form at 24 slots)
+# phase X from the maintained products (the automatic form) and by dot
+# products (asked for)
 PLANS_256 = [(50, False, 6), (52, True, 6), (58, False, 8), (60, True, 8),
              (70, False, 12), (66, True, 12), (80, False, 16), (78, True, 16),
              (96, False, 24), (90, True, 24)]
@@ -86,7 +85,7 @@ def test_many_walk_plans_int8(n, sym, slots, phase_x):
     F, D = instances.uniform_instance(n, 600 + n, symmetric=sym)
     tn = instances.periodic_tenure(n)
     iters = 400
-    products = int(phase_x == q.PHASE_X_AUTO and slots <= 16)
+    products = int(phase_x == q.PHASE_X_AUTO)
     with q.Instance(F, D) as inst:
         assert inst.info["delta_bytes"] == 4
         prm = q.make_params(W, seed=31, iters=iters, tenure=tn, descend=True, phase_x=phase_x)
@@ -145,3 +144,23 @@ def test_512x26_plan(n, sym, scale, int64):
         assert (plan["threads_per_walk"], plan["pairs_per_thread"]) == (512, 26), plan
         g = inst.search(prm)
     check_rows(g, F, D, [0, 1, 2], seed=34, iters=300, tenure=tn, descend=True)
+
+
+@pytest.mark.parametrize("phase_x", [q.PHASE_X_AUTO, q.PHASE_X_DOTS])
+@pytest.mark.parametrize("n,sym,slots", [(104, False, 12), (110, True, 16), (127, False, 20),
+                                         (131, True, 20), (139, False, 24), (144, True, 24)])
+def test_512_thread_plans_int8(n, sym, slots, phase_x):
+    """The 512-thread int8 plans of n = 101-146 (one walk per SM), with phase
+    X from the maintained products (the automatic form, up to 24 slots) and
+    by dot products: sampled walks equal the oracle's."""
+    F, D = instances.uniform_instance(n, 1100 + n, symmetric=sym)
+    tn = instances.periodic_tenure(n)
+    with q.Instance(F, D) as inst:
+        assert inst.info["delta_bytes"] == 4
+        prm = q.make_params(4, seed=35, iters=300, tenure=tn, descend=True,
+                            threads_per_walk=512, phase_x=phase_x)
+        plan = inst.plan(prm)
+        assert (plan["threads_per_walk"], plan["pairs_per_thread"]) == (512, slots), plan
+        assert plan["products"] == int(phase_x == q.PHASE_X_AUTO), plan
+        g = inst.search(prm)
+    check_rows(g, F, D, [0, 1, 2, 3], seed=35, iters=300, tenure=tn, descend=True)
