@@ -169,6 +169,10 @@ def profile_figures(name, kernel_hash):
     return out
 
 
+def phase_x_of(q, args):
+    return q.PHASE_X_DOTS if args.phase_x == "dots" else q.PHASE_X_AUTO
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -349,7 +353,7 @@ def measure_asym50(args, q, stream, flush, dev, world, rank, khash, baselines=Tr
     inst = q.Instance(w["F"], w["D"])
     prm = q.make_params(W, seed=w["seed"], iters=iters, tenure=w["tenure"], aspiration=True,
                         walk_base=replica_walk_base(rank, W),
-                        threads_per_walk=args.threads_per_walk)
+                        threads_per_walk=args.threads_per_walk, phase_x=phase_x_of(q, args))
     plan = inst.plan(prm)
     outs = inst.device_outputs(W, device=dev)
     step = lambda: inst.search_async(prm, outs, stream=stream)  # noqa: E731
@@ -390,7 +394,8 @@ def measure_asym50(args, q, stream, flush, dev, world, rank, khash, baselines=Tr
         # plain form: one launch per walk (same kernel body), one step
         pprm = q.make_params(W, seed=w["seed"], iters=iters, tenure=w["tenure"],
                              aspiration=True, walk_base=replica_walk_base(rank, W),
-                             launch=q.LAUNCH_PLAIN, threads_per_walk=args.threads_per_walk)
+                             launch=q.LAUNCH_PLAIN, threads_per_walk=args.threads_per_walk,
+                             phase_x=phase_x_of(q, args))
         pouts = inst.device_outputs(W, device=dev)
         with torch.cuda.stream(stream):
             inst.search_async(pprm, pouts, stream=stream)  # warm-up
@@ -452,7 +457,7 @@ def measure_grid100(args, q, stream, flush, dev, world, rank, khash, baselines=T
     iters = args.iters or w["iters"]
     inst = q.Instance(w["F"], w["D"])
     prm = q.make_params(W, seed=w["seed"], iters=iters, tenure=w["tenure"], descend=True,
-                        walk_base=replica_walk_base(rank, W))
+                        walk_base=replica_walk_base(rank, W), phase_x=phase_x_of(q, args))
     outs = inst.device_outputs(W, device=dev)
     with torch.cuda.stream(stream):
         inst.search_async(prm, outs, stream=stream)
@@ -527,7 +532,7 @@ def measure_batch512(args, q, stream, flush, dev, world, rank, khash, baselines=
     b = q.Batch(Fs, Ds, force_int64=True)
     tenure = (90, 110, 200)  # [0.9n, 1.1n] every 2n, per instance
     prm = q.make_params(W, seed=w["seed"], iters=iters, tenure=tenure, tenure_per_n=True,
-                        walk_base=replica_walk_base(rank, W))
+                        walk_base=replica_walk_base(rank, W), phase_x=phase_x_of(q, args))
     t0 = time.perf_counter()
     tune = [] if args.no_tune else b.autotune(prm, trial_iters=max(50, iters // 20))
     tune_s = time.perf_counter() - t0
@@ -774,6 +779,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true",
                     help="batch512: the rule's plans, without the autotuner (profiling)")
     ap.add_argument("--threads-per-walk", type=int, default=0)
+    ap.add_argument("--phase-x", choices=["auto", "dots"], default="auto",
+                    help="phase X from maintained products where they apply (auto) or by "
+                         "dot products")
     ap.add_argument("--iters", type=int, default=0,
                     help="override the iteration count (smaller cases for profiling)")
     ap.add_argument("--walks", type=int, default=0, help="override the walk count")

@@ -116,8 +116,8 @@ typedef struct {
  * recomputed by Eq. 2) gets its dot products (qap_search_params.phase_x):
  *   QAP_PHASE_X_AUTO  the n x n products M[x][k] = F[x].P[k] + F^T[x].P^T[k]
  *                     kept in shared memory and brought up to date by a
- *                     rank-2 update per move, where they apply: int8 flow
- *                     storage, int32 deltas, plans of at most 24 pairs per
+ *                     rank-2 update per move, where they apply: int8 or
+ *                     int16 flow storage, plans of at most 24 pairs per
  *                     thread (12 at 1024 threads), and an M that fits shared
  *                     memory (and still lets two walks share an SM where the
  *                     plan was taken for that); elsewhere dot products;
@@ -278,7 +278,7 @@ typedef struct {
   int32_t classes;           /* launches of a batch search (size classes);
                                 1 for one instance                          */
   int32_t products;          /* 1: phase X from products kept in shared
-                                memory (int8 flows, when they fit)          */
+                                memory (int8 or int16 flows, when they fit) */
   int32_t workspace;         /* 1: deltas and marks in the device workspace */
 } qap_plan_info;
 qap_status qap_plan(qap_ctx* ctx, const qap_search_params* params, qap_plan_info* out);

@@ -21,7 +21,9 @@ LIB = os.path.join(BUILD, "libqap.so")
 UNITS = ["qap_api.cu", "qap_walk_i32_f8.cu", "qap_walk_i32_f8m.cu", "qap_walk_i32_f16.cu",
          "qap_walk_i64_f16.cu", "qap_batch_i32_f8.cu", "qap_batch_i32_f8m.cu",
          "qap_batch_i32_f16.cu", "qap_batch_i64_f16.cu", "qap_walk_i64_f64.cu",
-         "qap_walk_i64_f64p.cu", "qap_batch_i64_f64.cu", "qap_batch_i64_f64p.cu", "qap_server.cu"]
+         "qap_walk_i64_f64p.cu", "qap_batch_i64_f64.cu", "qap_batch_i64_f64p.cu", "qap_server.cu",
+         "qap_walk_i32_f16m.cu", "qap_walk_i64_f16m.cu", "qap_batch_i32_f16m.cu",
+         "qap_batch_i64_f16m.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-Xcompiler", "-pthread", "-I", INCLUDE]

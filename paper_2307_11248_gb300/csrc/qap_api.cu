@@ -766,8 +766,7 @@ qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
         cands.push_back(p);
         Plan m = p;
         m.store |= qapk::kProductM;
-        if (tp.phase_x != QAP_PHASE_X_DOTS && b->fbytes == 1 && b->dbytes == 4 &&
-            has_product_form(p) && fits(m))
+        if (tp.phase_x != QAP_PHASE_X_DOTS && b->fbytes != 8 && has_product_form(p) && fits(m))
           cands.push_back(m);
       }
     }

@@ -5,6 +5,8 @@
 
 namespace qapk {
 
+BatchKernelFn batch_kernel_i32_f16m(int nt, int maxpt, int store);  // qap_batch_i32_f16m.cu
+
 #define QAP_PLANS(K)                                             \
   switch (nt * 1000 + maxpt * 10 + store) {                      \
     case 128040: return K<DT, FE, 128, 4, 0>;                    \
@@ -33,6 +35,7 @@ namespace qapk {
 BatchKernelFn batch_kernel_i32_f16(int nt, int maxpt, int store) {
   using DT = int32_t;
   using FE = int16_t;
+  if (store & kProductM) return batch_kernel_i32_f16m(nt, maxpt, store);
   QAP_PLANS(batch_kernel)
 }
 

@@ -246,7 +246,7 @@ inline int plan_smem(const Plan& p, const DevInstance* d, int count, int fbytes,
   return smem;
 }
 
-// Register plans compiled with the maintained products M (int8 flows): up
+// Register plans compiled with the maintained products M (int8 and int16 flows): up
 // to 24 slots (12 at 1024 threads).  Measured against the dot products at
 // 24 slots: the n = 100 grid 153.5 -> 150.9 ms per step, asymmetric n = 96
 // (2 walks per SM) 14.2 -> 12.8 ms, n = 135 at 512 x 24 15.0 -> 13.2 ms; at
@@ -255,9 +255,9 @@ inline bool has_product_form(const Plan& p) {
   return p.store == 0 && (p.nt == 1024 ? p.maxpt <= 12 : p.maxpt <= 24);
 }
 
-// The products form of a register plan when the flows are int8 and M fits
-// shared memory too (phase X then reads M instead of computing dot
-// products), unless the caller asks for the dot products.  Measured with
+// The products form of a register plan when the flows are stored as int8 or
+// int16 and M fits shared memory too (phase X then reads M instead of
+// computing dot products), unless the caller asks for the dot products.  Measured with
 // 2 walks per SM, 4000 iterations: asymmetric n = 60 / 70 / 80 8.4 / 10.4 /
 // 12.9 ms against 10.3 / 11.0 / 13.4 for symmetric ones by dot products;
 // symmetric n = 50 / 60 / 70 / 80 by products 6.7 / 8.4 / 10.3 / 12.7 ms;
@@ -265,7 +265,7 @@ inline bool has_product_form(const Plan& p) {
 // compiled with M) the n = 100 grid took 157.8 against 154.2 ms.
 inline Plan with_products(Plan p, const DevInstance* d, int count, int fbytes, int dbytes,
                           int smem_optin, int reserve, int form) {
-  if (form == QAP_PHASE_X_DOTS || fbytes != 1 || dbytes != 4 || !has_product_form(p)) return p;
+  if (form == QAP_PHASE_X_DOTS || fbytes == 8 || !has_product_form(p)) return p;
   Plan m = p;
   m.store |= qapk::kProductM;
   return plan_smem(m, d, count, fbytes, dbytes) + reserve <= smem_optin ? m : p;

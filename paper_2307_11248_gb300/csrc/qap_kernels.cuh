@@ -120,7 +120,7 @@ struct BatchArgs {
 // F^T from global memory (L1-cached), leaving shared memory to P and P^T.
 constexpr int kGlobalDelta = 1;
 constexpr int kGlobalFlow = 2;
-// Plans with bit kProductM (int8 flows) keep the n x n products
+// Plans with bit kProductM (int8 or int16 flows) keep the n x n products
 //   M[x][k] = sum_j F[x][j] P[k][j] + F[j][x] P[j][k]
 // in shared memory, their columns indexed by unit (see compute_m), and
 // update them after each move (see phase_m_update), so that phase X reads
@@ -134,6 +134,10 @@ constexpr int kGlobalP = 8;
 // row stride of M in int32 words: whole 16-byte groups, an odd number of
 // them (rows read side by side by consecutive threads spread over banks)
 __host__ __device__ inline int ld_m(int n) { return 4 * (((n + 3) / 4) | 1); }
+// int32 words per index of the products form's update vectors: int8 flows
+// pack (b, e, a, c) into one word; int16 flows keep (a, c) and (b, e) as
+// int32 pairs (differences of int16 values need 17 bits)
+__host__ __device__ constexpr int m_words(int fbytes) { return fbytes == 1 ? 1 : 2; }
 
 // ---------------------------------------------------------------------------
 // shared-memory layout (host and device agree through this function)
@@ -172,8 +176,9 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int ldF, int fbytes, in
   L.offRedD = o; o = align16(o + 32 * 8);
   L.offRedK = o; o = align16(o + 32 * 4);
   L.offSum = o;  o = align16(o + 32 * 8);
-  // M, the update words by index and by unit, and sigma (see compute_m)
-  L.offM = o;    o = (store & kProductM) ? align16(o + ((n + 2) * ld_m(n) + n) * 4) : o;
+  // M, the update words by index and by label, and sigma (see compute_m)
+  L.offM = o;
+  o = (store & kProductM) ? align16(o + ((n + 2 * m_words(fbytes)) * ld_m(n) + n) * 4) : o;
   L.bytes = o;
   return L;
 }
@@ -237,8 +242,8 @@ template <> struct Chunk<int64_t> {
 };
 
 // ---------------------------------------------------------------------------
-// O(1)-update vectors (a, b, c, e) of one index: four int16 in 8 bytes when
-// the flows are int8 (every entry then lies in [-255, 255]), else four int32
+// O(1)-update vectors (a, b, c, e) of one index: four bytes and one int32
+// in 8 bytes when the flows are int8 (see VecOps<int8_t>), else four int32
 // ---------------------------------------------------------------------------
 template <typename FE> struct VecOps;
 
@@ -407,7 +412,7 @@ struct WalkSmem {
   DT* redD;
   uint32_t* redK;
   int64_t* sum;
-  int32_t* M;  // kProductM plans: M (n x ld_m(n)), two rows of ld_m(n) update words, sigma (n)
+  int32_t* M;  // kProductM plans: M (n x ld_m(n)), update words by index and by label, sigma (n)
 };
 
 // Eq. 2 (with the diagonal term) for the pair {x, k}, by one thread, from the
@@ -610,7 +615,7 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
 }
 
 // ---------------------------------------------------------------------------
-// Phase X from maintained products (plans with kProductM, int8 flows)
+// Phase X from maintained products (plans with kProductM, int8 or int16 flows)
 // ---------------------------------------------------------------------------
 // These plans neither exchange rows and columns of P nor index M by
 // location.  P keeps the walk's starting matrix P0 = D[p0][p0], and
@@ -627,17 +632,17 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
 
 // Mt from P0 at the start of a walk (sigma the identity): one dot product
 // per entry (two when F or D is asymmetric).  Mt[k][k] is g[k].
-template <int NT>
-__device__ __forceinline__ void compute_m(const WalkSmem<int32_t, int8_t>& S, int32_t* Mt, int n,
-                                          int ldF, int ldP, bool sym) {
-  using C = Chunk<int8_t>;
+template <int NT, typename DT, typename FE>
+__device__ __forceinline__ void compute_m(const WalkSmem<DT, FE>& S, int32_t* Mt, int n, int ldF,
+                                          int ldP, bool sym) {
+  using C = Chunk<FE>;
   const int nc = (n + C::W - 1) / C::W, ldm = ld_m(n);
   for (int e = threadIdx.x; e < n * n; e += NT) {
     const int x = e / n, k = e - (e / n) * n;
-    const auto* Fx = reinterpret_cast<const C::FV*>(S.F + x * ldF);
-    const auto* Pk = reinterpret_cast<const C::QV*>(S.P + k * ldP);
-    const auto* Ftx = reinterpret_cast<const C::FV*>(S.Ft + x * ldF);
-    const auto* Ptk = reinterpret_cast<const C::QV*>(S.Pt + k * ldP);
+    const auto* Fx = reinterpret_cast<const typename C::FV*>(S.F + x * ldF);
+    const auto* Pk = reinterpret_cast<const typename C::QV*>(S.P + k * ldP);
+    const auto* Ftx = reinterpret_cast<const typename C::FV*>(S.Ft + x * ldF);
+    const auto* Ptk = reinterpret_cast<const typename C::QV*>(S.Pt + k * ldP);
     int acc = 0;
     for (int c = 0; c < nc; ++c) {
       acc = C::dot(Fx[c], Pk[c], acc);
@@ -648,20 +653,22 @@ __device__ __forceinline__ void compute_m(const WalkSmem<int32_t, int8_t>& S, in
 }
 
 // Phase X of move (r, s) from Mt (pre-move): one thread per index k writes
-// the update vector of k, also as one word by index (vw[k], whose bytes a_k,
-// c_k phase_m_update reads per row) and by label (vwu[sigma[k]], its b_k,
-// e_k per column), and, for k outside {r, s}, the recomputed deltas of the
+// the update vector of k, also by index (vw, whose a_k, c_k phase_m_update
+// reads per row) and by label (vwu at sigma[k], whose b_k, e_k it reads per
+// column): int8 flows store the packed word in both, int16 flows the int32
+// pairs (a_k, c_k) and (b_k, e_k); and, for k outside {r, s}, the recomputed
+// deltas of the
 // pairs {r, k} and {s, k}, whose dot products are the entries
 //   F[r].Q[k] + F^T[r].Q^T[k] = M[r][k],  F[k].Q[s] + F^T[k].Q^T[s] = M[k][s]
 // (and the same with r, s exchanged); the threads of k = r and k = s write
 // g'[r] = M'[r][r] = M[r][s] - a_r b_s - c_r e_s and g'[s] likewise.  Q is
 // read from P0 through sigma.  The finish is the one of phase_x.
-template <typename DT, int NT, typename VO>
-__device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, int8_t>& S, const int32_t* Mt,
+template <typename DT, typename FE, int NT, typename VO>
+__device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, FE>& S, const int32_t* Mt,
                                              int32_t* vw, int32_t* vwu, const int32_t* sigma,
                                              DT* gn, int n, int ldF, int ldP, int r, int s) {
-  const int8_t* F = S.F;
-  const int8_t* Ft = S.Ft;
+  const FE* F = S.F;
+  const FE* Ft = S.Ft;
   const int8_t* P0 = S.P;
   const int8_t* P0t = S.Pt;
   const int ldm = ld_m(n);
@@ -679,8 +686,13 @@ __device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, int8_t>& S, cons
     const int a = Frk - Fsk, b = Qrk - Qsk, c = Fkr - Fks, e = Qkr - Qks;
     const typename VO::V v = VO::pack(a, b, c, e);
     VO::put(S.vec, n, k, v);
-    vw[k] = v.x;
-    vwu[uk] = v.x;
+    if constexpr (sizeof(FE) == 1) {
+      vw[k] = v.x;
+      vwu[uk] = v.x;
+    } else {
+      reinterpret_cast<int2*>(vw)[k] = make_int2(a, c);
+      reinterpret_cast<int2*>(vwu)[uk] = make_int2(b, e);
+    }
     if (k == r || k == s) {
       // g'[x] = M[x][xb] - c_x e_xb - a_x b_xb, xb the other of r, s
       const int uxb = k == s ? ur : us;
@@ -730,26 +742,44 @@ __device__ __forceinline__ MShare m_share(int n, int nt) {
 }
 
 // Mt after move (r, s), in place, with the update words of phase_m_prep:
-//   Mt'[x][f] -= (a_x, c_x) . (b_j, e_j),  j the location of unit f before
-// the move, as one dp4a of the bytes (a_x, c_x, 0, 0) of vw[x] with vwu[f]
-// = (b_j, e_j, a_j, c_j).  Runs after the owner pass, which does not read
-// Mt; phase_m_prep of this move read it before the barrier that precedes
-// the owner pass, and the next one reads it after the next arg-min's
-// barrier.  Columns past n are padding.
+//   Mt'[x][u] -= (a_x, c_x) . (b_j, e_j),  j the location of label u before
+// the move.  int8 flows: one dp4a of the bytes (a_x, c_x, 0, 0) of vw[x]
+// with vwu[u] = (b_j, e_j, a_j, c_j); int16 flows: two multiply-adds of the
+// int32 pairs.  Runs after the owner pass, which does not read Mt;
+// phase_m_prep of this move read it before the barrier that precedes the
+// owner pass, and the next one reads it after the next arg-min's barrier.
+// Columns past n are padding.
+template <typename FE>
 __device__ __forceinline__ void phase_m_update(int32_t* Mt, const int32_t* vw,
                                                const int32_t* vwu, int n, MShare sh) {
   if (sh.x0 >= sh.rows) return;
   const int ldm = ld_m(n);
-  const int4 w = reinterpret_cast<const int4*>(vwu)[sh.g];
-  for (int x = sh.x0; x < n; x += sh.rows) {
-    const int ux = (int)__byte_perm((uint32_t)vw[x], 0u, 0x4432u);
-    int4* Mx = reinterpret_cast<int4*>(Mt + x * ldm) + sh.g;
-    int4 m = *Mx;
-    m.x -= __dp4a(ux, w.x, 0);
-    m.y -= __dp4a(ux, w.y, 0);
-    m.z -= __dp4a(ux, w.z, 0);
-    m.w -= __dp4a(ux, w.w, 0);
-    *Mx = m;
+  if constexpr (sizeof(FE) == 1) {
+    const int4 w = reinterpret_cast<const int4*>(vwu)[sh.g];
+    for (int x = sh.x0; x < n; x += sh.rows) {
+      const int ux = (int)__byte_perm((uint32_t)vw[x], 0u, 0x4432u);
+      int4* Mx = reinterpret_cast<int4*>(Mt + x * ldm) + sh.g;
+      int4 m = *Mx;
+      m.x -= __dp4a(ux, w.x, 0);
+      m.y -= __dp4a(ux, w.y, 0);
+      m.z -= __dp4a(ux, w.z, 0);
+      m.w -= __dp4a(ux, w.w, 0);
+      *Mx = m;
+    }
+  } else {
+    // (b, e) of the group's 4 labels
+    const int4 w0 = reinterpret_cast<const int4*>(vwu)[2 * sh.g];
+    const int4 w1 = reinterpret_cast<const int4*>(vwu)[2 * sh.g + 1];
+    for (int x = sh.x0; x < n; x += sh.rows) {
+      const int2 ac = reinterpret_cast<const int2*>(vw)[x];
+      int4* Mx = reinterpret_cast<int4*>(Mt + x * ldm) + sh.g;
+      int4 m = *Mx;
+      m.x -= ac.x * w0.x + ac.y * w0.y;
+      m.y -= ac.x * w0.z + ac.y * w0.w;
+      m.z -= ac.x * w1.x + ac.y * w1.y;
+      m.w -= ac.x * w1.z + ac.y * w1.w;
+      *Mx = m;
+    }
   }
 }
 
@@ -1006,10 +1036,11 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   // maintained products (columns by unit), the update words by index and
   // by unit, and this thread's share of the update (held across the walk,
   // except at 1024 threads, whose 64 registers spill it)
+  constexpr int kMW = m_words((int)sizeof(FE));
   int32_t* const Mt = S.M;
   int32_t* const vw = S.M ? S.M + n * ld_m(n) : nullptr;
-  int32_t* const vwu = S.M ? vw + ld_m(n) : nullptr;
-  int32_t* const sigma = S.M ? vwu + ld_m(n) : nullptr;
+  int32_t* const vwu = S.M ? vw + kMW * ld_m(n) : nullptr;
+  int32_t* const sigma = S.M ? vwu + kMW * ld_m(n) : nullptr;
   [[maybe_unused]] const MShare msh = NT < 1024 ? m_share(n, NT) : MShare{};
   if constexpr ((STORE & kProductM) != 0) {
     for (int x = tid; x < n; x += NT) sigma[x] = x;
@@ -1226,7 +1257,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   // by dot products over the rows of F and P.
   auto phase_x_any = [&](int r, int s) {
     if constexpr ((STORE & kProductM) != 0)
-      phase_m_prep<DT, NT, VOsel>(S, Mt, vw, vwu, sigma, gn, n, ldF, ldP, r, s);
+      phase_m_prep<DT, FE, NT, VOsel>(S, Mt, vw, vwu, sigma, gn, n, ldF, ldP, r, s);
     else
       phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
   };
@@ -1260,7 +1291,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         // Mt after the move (read by the next phase X, after the next
         // arg-min's barrier); after the owner pass, so that each thread's
         // candidate is ready first (asym50 10.14 -> 10.04 ms per step)
-        phase_m_update(Mt, vw, vwu, n, NT < 1024 ? msh : m_share(n, NT));
+        phase_m_update<FE>(Mt, vw, vwu, n, NT < 1024 ? msh : m_share(n, NT));
       }
       DT* t = gc; gc = gn; gn = t;
     }
@@ -1402,7 +1433,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         // Mt after the move (read by the next phase X, after the next
         // arg-min's barrier); after the owner pass, so that each thread's
         // candidate is ready first (asym50 10.14 -> 10.04 ms per step)
-        phase_m_update(Mt, vw, vwu, n, NT < 1024 ? msh : m_share(n, NT));
+        phase_m_update<FE>(Mt, vw, vwu, n, NT < 1024 ? msh : m_share(n, NT));
       }
       DT* t = gc; gc = gn; gn = t;
     }

@@ -171,11 +171,10 @@ void check_choose_plan_fit() {
           if (!compiled_register_plan(reg)) fail("not a compiled plan", n, 0, many, p);
           if (!fits(n, p)) fail("plan does not hold n", n, 0, many, p);
           if (p.store & qapk::kProductM) {
-            if (fbytes != 1 || dbytes != 4 || form == QAP_PHASE_X_DOTS)
+            if (fbytes == 8 || form == QAP_PHASE_X_DOTS)
               fail("products form where it does not apply", n, 0, many, p);
             if (!qaph::has_product_form(reg)) fail("products form not compiled", n, 0, many, p);
-          } else if (form == QAP_PHASE_X_AUTO && fbytes == 1 && dbytes == 4 &&
-                     qaph::has_product_form(reg)) {
+          } else if (form == QAP_PHASE_X_AUTO && fbytes != 8 && qaph::has_product_form(reg)) {
             // left out only where M does not fit, or keeps two walks from
             // sharing an SM where the plan was taken for that
             Plan m = reg;

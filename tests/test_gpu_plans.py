@@ -97,19 +97,29 @@ def test_many_walk_plans_int8(n, sym, slots, phase_x):
                descend=True)
 
 
-@pytest.mark.parametrize("n,sym,slots", [(58, False, 8), (70, False, 12), (80, True, 16),
-                                         (96, False, 24)])
-def test_many_walk_plans_int16_flows(n, sym, slots):
-    """Flows beyond a byte take the int16 element path (interleaved slots)."""
+@pytest.mark.parametrize("phase_x", [q.PHASE_X_AUTO, q.PHASE_X_DOTS])
+# (n, symmetric, slots, int64 deltas, products in the automatic form): at
+# n = 96 asymmetric M would keep two walks from sharing an SM, so the
+# automatic form stays with the dot products there
+@pytest.mark.parametrize("n,sym,slots,int64,prod", [
+    (58, False, 8, False, 1), (70, False, 12, False, 1), (80, True, 16, False, 1),
+    (92, True, 24, False, 1), (96, False, 24, False, 0), (52, True, 6, True, 1),
+    (66, False, 12, True, 1), (90, True, 24, True, 1)])
+def test_many_walk_plans_int16_flows(n, sym, slots, int64, prod, phase_x):
+    """Flows beyond a byte take the int16 element path (interleaved slots),
+    with int32 or int64 deltas, phase X from the maintained products (the
+    automatic form, when they fit shared memory) or by dot products."""
     W = 2 * sms()
     F, D = instances.uniform_instance(n, 700 + n, symmetric=sym, hi=99)
     F = F * 20  # up to 1980: int16 flows, still int32 deltas
     tn = instances.periodic_tenure(n)
-    with q.Instance(F, D) as inst:
-        assert inst.info["delta_bytes"] == 4
-        prm = q.make_params(W, seed=32, iters=300, tenure=tn)
+    with q.Instance(F, D, force_int64=int64) as inst:
+        assert inst.info["delta_bytes"] == (8 if int64 else 4)
+        assert inst.info["flow_bytes"] == 2
+        prm = q.make_params(W, seed=32, iters=300, tenure=tn, phase_x=phase_x)
         plan = inst.plan(prm)
         assert plan["threads_per_walk"] == 256 and plan["pairs_per_thread"] == slots, plan
+        assert plan["products"] == (prod if phase_x == q.PHASE_X_AUTO else 0), plan
         g = inst.search(prm)
     check_rows(g, F, D, [1, W // 3, W - 2], seed=32, iters=300, tenure=tn)
 

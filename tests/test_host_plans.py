@@ -2,8 +2,8 @@
 tests/host_plan_rules.cu (host code only, no CUDA calls) with nvcc and runs
 it.  It checks, for every n and instance kind, that the chosen plan holds n,
 fits shared memory, is compiled into the library and follows the stated
-preferences (the products form for int8 flows with int32 deltas wherever
-it is compiled and fits, unless the dot products are asked for, and nowhere
+preferences (the products form for int8 and int16 flows wherever it is
+compiled and fits, unless the dot products are asked for, and nowhere
 else; 256 threads with many slots only when the walks fill two CTAs per SM,
 and then two CTAs fit an SM)."""
 import os
