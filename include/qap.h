@@ -120,7 +120,9 @@ typedef struct {
  *                     int16 flow storage, plans of at most 24 pairs per
  *                     thread (12 at 1024 threads), and an M that fits shared
  *                     memory (and still lets two walks share an SM where the
- *                     plan was taken for that); elsewhere dot products;
+ *                     plan was taken for that), if need be without the
+ *                     transposed copies of F and P (their entries then read
+ *                     from columns); elsewhere dot products;
  *   QAP_PHASE_X_DOTS  dot products over the rows of F and P at every move.
  * Both give the same walks; qap_plan reports which one runs. */
 #define QAP_PHASE_X_AUTO 0
@@ -277,8 +279,12 @@ typedef struct {
   int32_t sms;
   int32_t classes;           /* launches of a batch search (size classes);
                                 1 for one instance                          */
-  int32_t products;          /* 1: phase X from products kept in shared
-                                memory (int8 or int16 flows, when they fit) */
+  int32_t products;          /* phase X: 0 by dot products; 1 from products
+                                kept in shared memory (int8 or int16 flows,
+                                when they fit); 2 the same without the
+                                transposed copies of F and P, whose entries
+                                are then read from columns (where M fits
+                                only so)                                    */
   int32_t workspace;         /* 1: deltas and marks in the device workspace */
 } qap_plan_info;
 qap_status qap_plan(qap_ctx* ctx, const qap_search_params* params, qap_plan_info* out);
@@ -349,7 +355,7 @@ typedef struct {
   int32_t threads_per_walk;  /* the plan kept                                */
   int32_t pairs_per_thread;
   int32_t workspace;         /* 1: deltas and marks in the device workspace  */
-  int32_t products;          /* 1: phase X from maintained products          */
+  int32_t products;          /* as in qap_plan_info                         */
   float trial_ms;            /* its trial time                               */
   float rule_ms;             /* the rule's plan's trial time                 */
 } qap_tune_result;
@@ -382,7 +388,7 @@ typedef struct {
   int32_t walks;             /* walks of the launch (instances x starts)     */
   int32_t threads_per_walk;
   int32_t pairs_per_thread;
-  int32_t products;          /* 1: phase X from maintained products          */
+  int32_t products;          /* as in qap_plan_info                         */
   int32_t workspace;         /* 1: deltas and marks in the device workspace  */
   int32_t grid;              /* CTAs of the launch                           */
   int32_t ctas_per_sm;

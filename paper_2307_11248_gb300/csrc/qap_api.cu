@@ -378,7 +378,7 @@ qap_status qap_plan(qap_ctx* ctx, const qap_search_params* params, qap_plan_info
   out->ctas_per_sm = L.ctas_per_sm;
   out->sms = ctx->sms;
   out->classes = 1;
-  out->products = (L.plan.store & qapk::kProductM) != 0;
+  out->products = products_form(L.plan);
   out->workspace = (L.plan.store & qapk::kGlobalDelta) != 0;
   return QAP_OK;
 }
@@ -644,7 +644,7 @@ qap_status qap_batch_plan(qap_batch* b, const qap_search_params* params, qap_pla
   out->ctas_per_sm = c.ctas_per_sm;
   out->sms = b->sms;
   out->classes = (int32_t)b->classes.size();
-  out->products = (c.plan.store & qapk::kProductM) != 0;
+  out->products = products_form(c.plan);
   out->workspace = (c.plan.store & qapk::kGlobalDelta) != 0;
   return QAP_OK;
 }
@@ -680,7 +680,7 @@ qap_status qap_batch_classes(qap_batch* b, const qap_search_params* params,
     o.walks = c.items;
     o.threads_per_walk = c.plan.nt;
     o.pairs_per_thread = c.plan.maxpt;
-    o.products = (c.plan.store & qapk::kProductM) != 0;
+    o.products = products_form(c.plan);
     o.workspace = (c.plan.store & qapk::kGlobalDelta) != 0;
     o.grid = c.grid;
     o.ctas_per_sm = c.ctas_per_sm;
@@ -764,10 +764,8 @@ qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
           fits(p = wide_store(p, dm.data(), (int)dm.size(), b->fbytes, b->dbytes,
                               b->smem_optin, 16))) {
         cands.push_back(p);
-        Plan m = p;
-        m.store |= qapk::kProductM;
-        if (tp.phase_x != QAP_PHASE_X_DOTS && b->fbytes != 8 && has_product_form(p) && fits(m))
-          cands.push_back(m);
+        const Plan m = with_products(p, b->fbytes, tp.phase_x, fits);
+        if (m.store != p.store) cands.push_back(m);
       }
     }
     if (qapk::row_segments(nmax, kLargePlan.maxpt) <= kLargePlan.nt) {
@@ -841,7 +839,7 @@ qap_status qap_batch_autotune(qap_batch* b, const qap_search_params* params,
       r.threads_per_walk = best.nt;
       r.pairs_per_thread = best.maxpt;
       r.workspace = (best.store & qapk::kGlobalDelta) != 0;
-      r.products = (best.store & qapk::kProductM) != 0;
+      r.products = products_form(best);
       r.trial_ms = best_ms;
       r.rule_ms = rule_ms;
     }

@@ -255,6 +255,14 @@ inline bool has_product_form(const Plan& p) {
   return p.store == 0 && (p.nt == 1024 ? p.maxpt <= 12 : p.maxpt <= 24);
 }
 
+// Products plans also compiled without the transposed copies of F and P
+// (kNoTransposed): the plans of the larger n, where M may not fit beside
+// them on asymmetric instances.
+inline bool has_notrans_form(const Plan& p) {
+  return p.store == 0 && ((p.nt == 256 && p.maxpt >= 12 && p.maxpt <= 24) ||
+                          (p.nt == 512 && p.maxpt >= 12 && p.maxpt <= 24));
+}
+
 // The products form of a register plan when the flows are stored as int8 or
 // int16 and M fits shared memory too (phase X then reads M instead of
 // computing dot products), unless the caller asks for the dot products.  Measured with
@@ -263,12 +271,24 @@ inline bool has_product_form(const Plan& p) {
 // symmetric n = 50 / 60 / 70 / 80 by products 6.7 / 8.4 / 10.3 / 12.7 ms;
 // n = 100 at 512 x 12 symmetric 10.2 against 12.1 ms.  At 24 slots (not
 // compiled with M) the n = 100 grid took 157.8 against 154.2 ms.
-inline Plan with_products(Plan p, const DevInstance* d, int count, int fbytes, int dbytes,
-                          int smem_optin, int reserve, int form) {
+// The form a plan reports: 0 dot products, 1 maintained products, 2 the
+// same without the transposed copies of F and P.
+inline int products_form(const Plan& p) {
+  return !(p.store & qapk::kProductM) ? 0 : (p.store & qapk::kNoTransposed) ? 2 : 1;
+}
+
+// Where M does not fit beside the transposed copies (or would keep two
+// walks from sharing an SM where the plan was taken for that), the form
+// without the copies.  `fits` says whether a plan fits.
+template <typename Fits>
+inline Plan with_products(Plan p, int fbytes, int form, Fits fits) {
   if (form == QAP_PHASE_X_DOTS || fbytes == 8 || !has_product_form(p)) return p;
   Plan m = p;
   m.store |= qapk::kProductM;
-  return plan_smem(m, d, count, fbytes, dbytes) + reserve <= smem_optin ? m : p;
+  if (fits(m)) return m;
+  if (!has_notrans_form(p)) return p;
+  m.store |= qapk::kNoTransposed;
+  return fits(m) ? m : p;
 }
 
 // The int64 element path reads F and F^T from global memory (L1-cached,
@@ -295,19 +315,19 @@ inline bool choose_plan_fit(int nmax, int threads, bool many, const DevInstance*
   if (nmax <= 181 && choose_plan(nmax, threads, many, &p)) {
     p = wide_store(p, d, count, fbytes, dbytes, smem_optin, reserve);
     if (plan_smem(p, d, count, fbytes, dbytes) + reserve <= smem_optin) {
-      Plan m = with_products(p, d, count, fbytes, dbytes, smem_optin, reserve, form);
-      if (many && threads == 0 && p.nt == 256 && p.maxpt > 8) {
-        // two CTAs per SM: each with its own 1 KB reserved by the hardware
-        auto two = [&](const Plan& x) {
-          return 2 * (plan_smem(x, d, count, fbytes, dbytes) + reserve + 1024) <=
-                 smem_optin + 1024;
-        };
-        if (!two(m)) m = p;
-        if (!two(m))
-          return choose_plan_fit(nmax, threads, false, d, count, fbytes, dbytes, smem_optin,
-                                 reserve, form, out);
-      }
-      *out = m;
+      const bool need_two = many && threads == 0 && p.nt == 256 && p.maxpt > 8;
+      // two CTAs per SM: each with its own 1 KB reserved by the hardware
+      auto two = [&](const Plan& x) {
+        return 2 * (plan_smem(x, d, count, fbytes, dbytes) + reserve + 1024) <=
+               smem_optin + 1024;
+      };
+      if (need_two && !two(p))
+        return choose_plan_fit(nmax, threads, false, d, count, fbytes, dbytes, smem_optin,
+                               reserve, form, out);
+      *out = with_products(p, fbytes, form, [&](const Plan& x) {
+        return plan_smem(x, d, count, fbytes, dbytes) + reserve <= smem_optin &&
+               (!need_two || two(x));
+      });
       return true;
     }
   }

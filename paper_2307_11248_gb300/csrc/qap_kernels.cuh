@@ -130,6 +130,10 @@ constexpr int kProductM = 4;
 // workspace (at SearchArgs::p_off) instead of shared memory; they read F and
 // F^T from global memory too.
 constexpr int kGlobalP = 8;
+// Products plans with bit kNoTransposed keep no transposed copies of F and P
+// in shared memory (room for M on large asymmetric instances): the few
+// transposed reads, at the start of a walk and in phase X, read columns.
+constexpr int kNoTransposed = 16;
 
 // row stride of M in int32 words: whole 16-byte groups, an odd number of
 // them (rows read side by side by consecutive threads spread over banks)
@@ -163,9 +167,10 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int ldF, int fbytes, in
   const int vbytes = fbytes == 8 ? 32 : 16; // update vector (a, b, c, e) of one index
   if (store & kGlobalDelta) slots = 0;
   L.offF = o;    o = fg ? o : align16(o + n * ldF * fbytes);
-  L.offFt = o;   o = (symF || fg) ? o : align16(o + n * ldF * fbytes);
+  const bool nt = store & kNoTransposed;
+  L.offFt = o;   o = (symF || fg || nt) ? o : align16(o + n * ldF * fbytes);
   L.offP = o;    o = pg ? o : align16(o + n * ldP * pbytes);
-  L.offPt = o;   o = (symD || pg) ? o : align16(o + n * ldP * pbytes);
+  L.offPt = o;   o = (symD || pg || nt) ? o : align16(o + n * ldP * pbytes);
   L.offTabu = o; o = align16(o + slots * 4);
   L.offVec = o;  o = align16(o + n * vbytes);
   L.offR = o;    o = align16(o + 2 * n * dbytes);
@@ -417,8 +422,9 @@ struct WalkSmem {
 
 // Eq. 2 (with the diagonal term) for the pair {x, k}, by one thread, from the
 // current P.  The column terms read the transposed copies so every access is
-// along a row.  Used for the initial deltas of a walk.
-template <typename DT, typename FE>
+// along a row (NOTR: no copies, the columns themselves, stride ld).  Used for
+// the initial deltas of a walk.
+template <typename DT, typename FE, bool NOTR>
 __device__ __forceinline__ DT delta_serial(const WalkSmem<DT, FE>& S, int n, int ldF, int ldP,
                                            bool sym, int x, int k) {
   using PE = typename Elem<FE>::P;
@@ -427,10 +433,11 @@ __device__ __forceinline__ DT delta_serial(const WalkSmem<DT, FE>& S, int n, int
   const FE* Fk = S.F + k * ldF;
   const PE* Px = S.P + x * ldP;
   const PE* Pk = S.P + k * ldP;
-  const FE* Ftx = S.Ft + x * ldF;
-  const FE* Ftk = S.Ft + k * ldF;
-  const PE* Ptx = S.Pt + x * ldP;
-  const PE* Ptk = S.Pt + k * ldP;
+  const FE* Ftx = NOTR ? S.F + x : S.Ft + x * ldF;
+  const FE* Ftk = NOTR ? S.F + k : S.Ft + k * ldF;
+  const PE* Ptx = NOTR ? S.P + x : S.Pt + x * ldP;
+  const PE* Ptk = NOTR ? S.P + k : S.Pt + k * ldP;
+  const int fs = NOTR ? ldF : 1, ps = NOTR ? ldP : 1;
   DT acc = 0;
   for (int j = 0; j < n; ++j) {
     if (j == x || j == k) continue;
@@ -438,7 +445,7 @@ __device__ __forceinline__ DT delta_serial(const WalkSmem<DT, FE>& S, int n, int
     if (sym) {
       acc += (DT)(2 * t1);
     } else {
-      const SC t2 = ((SC)Ftx[j] - (SC)Ftk[j]) * ((SC)Ptk[j] - (SC)Ptx[j]);
+      const SC t2 = ((SC)Ftx[j * fs] - (SC)Ftk[j * fs]) * ((SC)Ptk[j * ps] - (SC)Ptx[j * ps]);
       acc += (DT)t1 + (DT)t2;
     }
   }
@@ -631,8 +638,9 @@ __device__ __forceinline__ void phase_x(const WalkSmem<DT, FE>& S, const DT* gc,
 // and with no exchange of columns.
 
 // Mt from P0 at the start of a walk (sigma the identity): one dot product
-// per entry (two when F or D is asymmetric).  Mt[k][k] is g[k].
-template <int NT, typename DT, typename FE>
+// per entry (two when F or D is asymmetric; NOTR: the second over columns,
+// element by element).  Mt[k][k] is g[k].
+template <int NT, bool NOTR, typename DT, typename FE>
 __device__ __forceinline__ void compute_m(const WalkSmem<DT, FE>& S, int32_t* Mt, int n, int ldF,
                                           int ldP, bool sym) {
   using C = Chunk<FE>;
@@ -646,8 +654,10 @@ __device__ __forceinline__ void compute_m(const WalkSmem<DT, FE>& S, int32_t* Mt
     int acc = 0;
     for (int c = 0; c < nc; ++c) {
       acc = C::dot(Fx[c], Pk[c], acc);
-      if (!sym) acc = C::dot(Ftx[c], Ptk[c], acc);
+      if (!NOTR && !sym) acc = C::dot(Ftx[c], Ptk[c], acc);
     }
+    if (NOTR && !sym)
+      for (int j = 0; j < n; ++j) acc += (int)S.F[j * ldF + x] * (int)S.P[j * ldP + k];
     Mt[x * ldm + k] = sym ? 2 * acc : acc;
   }
 }
@@ -663,7 +673,7 @@ __device__ __forceinline__ void compute_m(const WalkSmem<DT, FE>& S, int32_t* Mt
 // (and the same with r, s exchanged); the threads of k = r and k = s write
 // g'[r] = M'[r][r] = M[r][s] - a_r b_s - c_r e_s and g'[s] likewise.  Q is
 // read from P0 through sigma.  The finish is the one of phase_x.
-template <typename DT, typename FE, int NT, typename VO>
+template <typename DT, typename FE, int NT, bool NOTR, typename VO>
 __device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, FE>& S, const int32_t* Mt,
                                              int32_t* vw, int32_t* vwu, const int32_t* sigma,
                                              DT* gn, int n, int ldF, int ldP, int r, int s) {
@@ -675,14 +685,17 @@ __device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, FE>& S, const in
   const int ur = sigma[r], us = sigma[s];  // P0 rows of locations r and s
   const int8_t* Qr = P0 + ur * ldP;         // Q[r][j] = Qr[sigma[j]]
   const int8_t* Qs = P0 + us * ldP;
-  const int8_t* Qtr = P0t + ur * ldP;       // Q^T[r][j] = Qtr[sigma[j]]
-  const int8_t* Qts = P0t + us * ldP;
+  // Q^T[r][j] = Qtr[sigma[j] * qs] (NOTR: column ur of P0)
+  const int8_t* Qtr = NOTR ? P0 + ur : P0t + ur * ldP;
+  const int8_t* Qts = NOTR ? P0 + us : P0t + us * ldP;
+  const int qs = NOTR ? ldP : 1;
   for (int k = threadIdx.x; k < n; k += NT) {
     const int uk = sigma[k];
     const int Frk = F[r * ldF + k], Fsk = F[s * ldF + k];
-    const int Fkr = Ft[r * ldF + k], Fks = Ft[s * ldF + k];
+    const int Fkr = NOTR ? F[k * ldF + r] : Ft[r * ldF + k];
+    const int Fks = NOTR ? F[k * ldF + s] : Ft[s * ldF + k];
     const int Qrk = Qr[uk], Qsk = Qs[uk];
-    const int Qkr = Qtr[uk], Qks = Qts[uk];
+    const int Qkr = Qtr[uk * qs], Qks = Qts[uk * qs];
     const int a = Frk - Fsk, b = Qrk - Qsk, c = Fkr - Fks, e = Qkr - Qks;
     const typename VO::V v = VO::pack(a, b, c, e);
     VO::put(S.vec, n, k, v);
@@ -696,7 +709,7 @@ __device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, FE>& S, const in
     if (k == r || k == s) {
       // g'[x] = M[x][xb] - c_x e_xb - a_x b_xb, xb the other of r, s
       const int uxb = k == s ? ur : us;
-      const int exb = Qtr[uxb] - Qts[uxb];
+      const int exb = Qtr[uxb * qs] - Qts[uxb * qs];
       const int bxb = Qr[uxb] - Qs[uxb];
       gn[k] = (DT)Mt[k * ldm + uxb] - (DT)(c * exb) - (DT)(a * bxb);
       continue;
@@ -896,14 +909,14 @@ __device__ __forceinline__ WalkSmem<DT, FE> smem_views(unsigned char* smem, cons
     S.Ft = const_cast<FE*>(reinterpret_cast<const FE*>(I.Ft));
   } else {
     S.F = reinterpret_cast<FE*>(smem + L.offF);
-    S.Ft = I.symF ? S.F : reinterpret_cast<FE*>(smem + L.offFt);
+    S.Ft = (I.symF || (STORE & kNoTransposed)) ? S.F : reinterpret_cast<FE*>(smem + L.offFt);
   }
   if (STORE & kGlobalP) {
     S.P = reinterpret_cast<PE*>(ws + p_off);
     S.Pt = I.symD ? S.P : S.P + (size_t)I.n * I.ldP;
   } else {
     S.P = reinterpret_cast<PE*>(smem + L.offP);
-    S.Pt = I.symD ? S.P : reinterpret_cast<PE*>(smem + L.offPt);
+    S.Pt = (I.symD || (STORE & kNoTransposed)) ? S.P : reinterpret_cast<PE*>(smem + L.offPt);
   }
   // workspace: deltas (NT * MAXPT x DT), then tabu stamps (NT * MAXPT x int32)
   S.tabu = (STORE & kGlobalDelta)
@@ -933,7 +946,7 @@ __device__ __forceinline__ void load_instance(const WalkSmem<DT, FE>& S, const I
   int4* sF = reinterpret_cast<int4*>(S.F);
   if (!(STORE & kGlobalFlow))
     for (int i = tid; i < nvec; i += NT) sF[i] = gF[i];
-  if (!I.symF && !(STORE & kGlobalFlow)) {
+  if (!I.symF && !(STORE & (kGlobalFlow | kNoTransposed))) {
     const int4* gFt = reinterpret_cast<const int4*>(I.Ft);
     int4* sFt = reinterpret_cast<int4*>(S.Ft);
     for (int i = tid; i < nvec; i += NT) sFt[i] = gFt[i];
@@ -941,7 +954,7 @@ __device__ __forceinline__ void load_instance(const WalkSmem<DT, FE>& S, const I
   const int pvec = I.n * I.ldP * (int)sizeof(typename Elem<FE>::P) / 16;
   int4* sP = reinterpret_cast<int4*>(S.P);
   for (int i = tid; i < pvec; i += NT) sP[i] = make_int4(0, 0, 0, 0);
-  if (!I.symD) {
+  if (!I.symD && !(STORE & kNoTransposed)) {
     int4* sPt = reinterpret_cast<int4*>(S.Pt);
     for (int i = tid; i < pvec; i += NT) sPt[i] = make_int4(0, 0, 0, 0);
   }
@@ -981,6 +994,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   const bool sym = I.symF && I.symD;
   const bool warp0 = tid < 32;
   constexpr bool kInterleave = interleaved<FE, NT>();
+  constexpr bool kNoTr = (STORE & kNoTransposed) != 0;
   // per-index vectors: the word-only form on the 6-slot products plan
   using VOsel = std::conditional_t<sizeof(FE) == 1 && (STORE & kProductM) != 0 && MAXPT == 6,
                                    VecOpsWord, VecOps<FE>>;
@@ -1021,7 +1035,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
     const int i = c / n, j = c - (c / n) * n;
     const PE v = Dg[(size_t)S.perm[i] * n + S.perm[j]];
     S.P[i * ldP + j] = v;
-    if (!I.symD) S.Pt[j * ldP + i] = v;
+    if (!I.symD && !kNoTr) S.Pt[j * ldP + i] = v;
   }
   for (int x = tid; x < n; x += NT) S.best[x] = S.perm[x];
   __syncthreads();
@@ -1044,7 +1058,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   [[maybe_unused]] const MShare msh = NT < 1024 ? m_share(n, NT) : MShare{};
   if constexpr ((STORE & kProductM) != 0) {
     for (int x = tid; x < n; x += NT) sigma[x] = x;
-    compute_m<NT>(S, Mt, n, ldF, ldP, sym);
+    compute_m<NT, kNoTr>(S, Mt, n, ldF, ldP, sym);
   }
   else
     compute_g<DT, FE, NT>(S, S.g0, n, ldF, ldP, sym, G);
@@ -1056,7 +1070,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   constexpr bool kSplitPass = !(STORE & kGlobalDelta);
 #pragma unroll
   for (int i = 0; i < MAXPT; ++i) {
-    dl.set(i, i < slen ? delta_serial<DT, FE>(S, n, ldF, ldP, sym, su, sv + i * sk)
+    dl.set(i, i < slen ? delta_serial<DT, FE, kNoTr>(S, n, ldF, ldP, sym, su, sv + i * sk)
                        : DeltaMax<DT>::v);
     S.tabu[i * NT + tid] = 0;
   }
@@ -1257,7 +1271,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   // by dot products over the rows of F and P.
   auto phase_x_any = [&](int r, int s) {
     if constexpr ((STORE & kProductM) != 0)
-      phase_m_prep<DT, FE, NT, VOsel>(S, Mt, vw, vwu, sigma, gn, n, ldF, ldP, r, s);
+      phase_m_prep<DT, FE, NT, kNoTr, VOsel>(S, Mt, vw, vwu, sigma, gn, n, ldF, ldP, r, s);
     else
       phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
   };

@@ -147,7 +147,7 @@ void check_choose_plan_fit() {
             continue;
           }
           if (p.store & qapk::kGlobalP) fail("P global on a narrow path", n, 0, many, p);
-          const int base = p.store & ~qapk::kProductM;
+          const int base = p.store & ~(qapk::kProductM | qapk::kNoTransposed);
           if (base != 0) {
             // the workspace plan: beyond the register plans' n, or where the
             // register plan the rules pick without the two-walks preference
@@ -170,18 +170,28 @@ void check_choose_plan_fit() {
           const Plan reg{p.nt, p.maxpt, 0};
           if (!compiled_register_plan(reg)) fail("not a compiled plan", n, 0, many, p);
           if (!fits(n, p)) fail("plan does not hold n", n, 0, many, p);
+          // the products form with the transposed copies where it fits, else
+          // without them where compiled and fitting, else the dot products
+          const bool two = many && p.nt == 256 && p.maxpt > 8;
+          auto fits_as = [&](int store) {
+            Plan m = reg;
+            m.store = store;
+            const int ms = qaph::plan_smem(m, &di, 1, fbytes, dbytes);
+            return ms + reserve <= optin && (!two || 2 * (ms + reserve + 1024) <= optin + 1024);
+          };
+          const int pm = qapk::kProductM, pn = qapk::kProductM | qapk::kNoTransposed;
           if (p.store & qapk::kProductM) {
             if (fbytes == 8 || form == QAP_PHASE_X_DOTS)
               fail("products form where it does not apply", n, 0, many, p);
             if (!qaph::has_product_form(reg)) fail("products form not compiled", n, 0, many, p);
+            if (p.store & qapk::kNoTransposed) {
+              if (!qaph::has_notrans_form(reg)) fail("no-transposes form not compiled", n, 0, many, p);
+              if (fits_as(pm)) fail("transposes left out where they fit", n, 0, many, p);
+            }
+          } else if (p.store & qapk::kNoTransposed) {
+            fail("no-transposes bit without products", n, 0, many, p);
           } else if (form == QAP_PHASE_X_AUTO && fbytes != 8 && qaph::has_product_form(reg)) {
-            // left out only where M does not fit, or keeps two walks from
-            // sharing an SM where the plan was taken for that
-            Plan m = reg;
-            m.store |= qapk::kProductM;
-            const int ms = qaph::plan_smem(m, &di, 1, fbytes, dbytes);
-            const bool two = many && p.nt == 256 && p.maxpt > 8;
-            if (ms + reserve <= optin && (!two || 2 * (ms + reserve + 1024) <= optin + 1024))
+            if (fits_as(pm) || (qaph::has_notrans_form(reg) && fits_as(pn)))
               fail("products form left out where it fits", n, 0, many, p);
           }
           if (p.nt == 256 && p.maxpt > 8) {

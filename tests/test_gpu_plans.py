@@ -98,12 +98,12 @@ def test_many_walk_plans_int8(n, sym, slots, phase_x):
 
 
 @pytest.mark.parametrize("phase_x", [q.PHASE_X_AUTO, q.PHASE_X_DOTS])
-# (n, symmetric, slots, int64 deltas, products in the automatic form): at
-# n = 96 asymmetric M would keep two walks from sharing an SM, so the
-# automatic form stays with the dot products there
+# (n, symmetric, slots, int64 deltas, products form in the automatic choice):
+# at n = 96 asymmetric M fits beside two walks per SM only without the
+# transposed copies of F and P (form 2)
 @pytest.mark.parametrize("n,sym,slots,int64,prod", [
     (58, False, 8, False, 1), (70, False, 12, False, 1), (80, True, 16, False, 1),
-    (92, True, 24, False, 1), (96, False, 24, False, 0), (52, True, 6, True, 1),
+    (92, True, 24, False, 1), (96, False, 24, False, 2), (52, True, 6, True, 1),
     (66, False, 12, True, 1), (90, True, 24, True, 1)])
 def test_many_walk_plans_int16_flows(n, sym, slots, int64, prod, phase_x):
     """Flows beyond a byte take the int16 element path (interleaved slots),
@@ -174,3 +174,23 @@ def test_512_thread_plans_int8(n, sym, slots, phase_x):
         assert plan["products"] == int(phase_x == q.PHASE_X_AUTO), plan
         g = inst.search(prm)
     check_rows(g, F, D, [0, 1, 2, 3], seed=35, iters=300, tenure=tn, descend=True)
+
+
+@pytest.mark.parametrize("n,fscale,int64", [(140, 20, True), (146, 1, False), (146, 20, False)])
+def test_products_without_transposed_copies(n, fscale, int64):
+    """Large asymmetric instances whose M fits shared memory only without the
+    transposed copies of F and P (products form 2: their entries read from
+    columns) on 512 x 24, int8 or int16 flows, int32 or int64 deltas: sampled
+    walks equal the oracle's."""
+    F, D = instances.uniform_instance(n, 1200 + n, symmetric=False)
+    F = F * fscale
+    tn = instances.periodic_tenure(n)
+    with q.Instance(F, D, force_int64=int64) as inst:
+        assert inst.info["flow_bytes"] == (2 if fscale > 1 or int64 else 1)
+        prm = q.make_params(3, seed=36, iters=300, tenure=tn, descend=True,
+                            threads_per_walk=512)
+        plan = inst.plan(prm)
+        assert (plan["threads_per_walk"], plan["pairs_per_thread"]) == (512, 24), plan
+        assert plan["products"] == 2, plan
+        g = inst.search(prm)
+    check_rows(g, F, D, [0, 1, 2], seed=36, iters=300, tenure=tn, descend=True)
