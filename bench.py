@@ -129,9 +129,10 @@ def gpu_uuid_of(dev):
     return u if u.startswith("GPU-") else f"GPU-{u}"
 
 
-# the sources of the kernels' code (the qap_walk_* / qap_batch_* units only
-# list which template instances exist)
-KERNEL_SOURCES = ("qap_kernels.cuh", "qap_philox.cuh")
+# the sources of the kernels' code and of the rules that pick a launch's
+# plan (the qap_walk_* / qap_batch_* units only list which template
+# instances exist)
+KERNEL_SOURCES = ("qap_kernels.cuh", "qap_philox.cuh", "qap_host.cuh")
 
 
 def kernel_source_hash():

@@ -118,7 +118,8 @@ typedef struct {
  *                     kept in shared memory and brought up to date by a
  *                     rank-2 update per move, where they apply: int8 or
  *                     int16 flow storage, plans of at most 24 pairs per
- *                     thread (12 at 1024 threads), and an M that fits shared
+ *                     thread (12 at 1024 threads; 26 at 512 threads with int16
+ *                     flows), and an M that fits shared
  *                     memory (and still lets two walks share an SM where the
  *                     plan was taken for that), if need be without the
  *                     transposed copies of F and P (their entries then read

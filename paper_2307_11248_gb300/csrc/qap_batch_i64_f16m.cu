@@ -29,6 +29,8 @@ namespace qapk {
     case 5121620: return K<DT, FE, 512, 16, kProductM | kNoTransposed>; \
     case 5122020: return K<DT, FE, 512, 20, kProductM | kNoTransposed>; \
     case 5122420: return K<DT, FE, 512, 24, kProductM | kNoTransposed>; \
+    case 5122604: return K<DT, FE, 512, 26, kProductM>;       \
+    case 5122620: return K<DT, FE, 512, 26, kProductM | kNoTransposed>; \
     default: return nullptr;                                     \
   }
 

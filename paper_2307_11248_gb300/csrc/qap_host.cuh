@@ -246,21 +246,24 @@ inline int plan_smem(const Plan& p, const DevInstance* d, int count, int fbytes,
   return smem;
 }
 
-// Register plans compiled with the maintained products M (int8 and int16 flows): up
-// to 24 slots (12 at 1024 threads).  Measured against the dot products at
-// 24 slots: the n = 100 grid 153.5 -> 150.9 ms per step, asymmetric n = 96
-// (2 walks per SM) 14.2 -> 12.8 ms, n = 135 at 512 x 24 15.0 -> 13.2 ms; at
-// 26 slots symmetric n = 148 was slower (14.0 -> 14.3 ms) and is left out.
-inline bool has_product_form(const Plan& p) {
-  return p.store == 0 && (p.nt == 1024 ? p.maxpt <= 12 : p.maxpt <= 24);
+// Register plans compiled with the maintained products M (int8 and int16
+// flows): up to 24 slots (12 at 1024 threads), and 512 x 26 for int16 flows.
+// Measured against the dot products at 24 slots: the n = 100 grid 153.5 ->
+// 150.9 ms per step, asymmetric n = 96 (2 walks per SM) 14.2 -> 12.8 ms,
+// n = 135 at 512 x 24 15.0 -> 13.2 ms; at 26 slots symmetric int8 n = 148
+// was slower (14.0 -> 14.3 ms), the int16 batch512 classes faster (step
+// 2799.6 -> 2782.4 ms).
+inline bool has_product_form(const Plan& p, int fbytes) {
+  if (p.store != 0) return false;
+  if (p.nt == 512 && p.maxpt == 26) return fbytes == 2;
+  return p.nt == 1024 ? p.maxpt <= 12 : p.maxpt <= 24;
 }
 
 // Products plans also compiled without the transposed copies of F and P
 // (kNoTransposed): the plans of the larger n, where M may not fit beside
 // them on asymmetric instances.
-inline bool has_notrans_form(const Plan& p) {
-  return p.store == 0 && ((p.nt == 256 && p.maxpt >= 12 && p.maxpt <= 24) ||
-                          (p.nt == 512 && p.maxpt >= 12 && p.maxpt <= 24));
+inline bool has_notrans_form(const Plan& p, int fbytes) {
+  return has_product_form(p, fbytes) && p.maxpt >= 12 && (p.nt == 256 || p.nt == 512);
 }
 
 // The products form of a register plan when the flows are stored as int8 or
@@ -282,11 +285,11 @@ inline int products_form(const Plan& p) {
 // without the copies.  `fits` says whether a plan fits.
 template <typename Fits>
 inline Plan with_products(Plan p, int fbytes, int form, Fits fits) {
-  if (form == QAP_PHASE_X_DOTS || fbytes == 8 || !has_product_form(p)) return p;
+  if (form == QAP_PHASE_X_DOTS || fbytes == 8 || !has_product_form(p, fbytes)) return p;
   Plan m = p;
   m.store |= qapk::kProductM;
   if (fits(m)) return m;
-  if (!has_notrans_form(p)) return p;
+  if (!has_notrans_form(p, fbytes)) return p;
   m.store |= qapk::kNoTransposed;
   return fits(m) ? m : p;
 }

@@ -183,15 +183,15 @@ void check_choose_plan_fit() {
           if (p.store & qapk::kProductM) {
             if (fbytes == 8 || form == QAP_PHASE_X_DOTS)
               fail("products form where it does not apply", n, 0, many, p);
-            if (!qaph::has_product_form(reg)) fail("products form not compiled", n, 0, many, p);
+            if (!qaph::has_product_form(reg, fbytes)) fail("products form not compiled", n, 0, many, p);
             if (p.store & qapk::kNoTransposed) {
-              if (!qaph::has_notrans_form(reg)) fail("no-transposes form not compiled", n, 0, many, p);
+              if (!qaph::has_notrans_form(reg, fbytes)) fail("no-transposes form not compiled", n, 0, many, p);
               if (fits_as(pm)) fail("transposes left out where they fit", n, 0, many, p);
             }
           } else if (p.store & qapk::kNoTransposed) {
             fail("no-transposes bit without products", n, 0, many, p);
-          } else if (form == QAP_PHASE_X_AUTO && fbytes != 8 && qaph::has_product_form(reg)) {
-            if (fits_as(pm) || (qaph::has_notrans_form(reg) && fits_as(pn)))
+          } else if (form == QAP_PHASE_X_AUTO && fbytes != 8 && qaph::has_product_form(reg, fbytes)) {
+            if (fits_as(pm) || (qaph::has_notrans_form(reg, fbytes) && fits_as(pn)))
               fail("products form left out where it fits", n, 0, many, p);
           }
           if (p.nt == 256 && p.maxpt > 8) {
