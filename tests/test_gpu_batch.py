@@ -33,13 +33,21 @@ def check_instance(g, inst_idx, W, F, D, **kw):
     assert np.array_equal(g["best_p"][rows, :n], o["best_p"]), (inst_idx, "best_p")
 
 
-def test_lognormal_batch_int64_bit_exact():
+@pytest.mark.parametrize("phase_x", [q.PHASE_X_AUTO, q.PHASE_X_DOTS])
+def test_lognormal_batch_int64_bit_exact(phase_x):
+    """Lognormal int16 flows with int64 deltas: the maintained-products
+    classes (automatic) and the dot-product ones (asked for) equal the
+    oracle."""
     insts = instances.batch_instances(10, 3)
     W, iters = 4, 300
     with q.Batch([i.F for i in insts], [i.D for i in insts], force_int64=True) as b:
         assert b.info["delta_bytes"] == 8 and b.info["count"] == 10
         tn = (20, 40, 60)
-        g = b.search(q.make_params(W, seed=1004, iters=iters, tenure=tn))
+        prm = q.make_params(W, seed=1004, iters=iters, tenure=tn, phase_x=phase_x)
+        classes, _ = b.classes(prm)
+        forms = {c["products"] for c in classes}
+        assert forms <= ({1, 2} if phase_x == q.PHASE_X_AUTO else {0}), forms
+        g = b.search(prm)
     for i, inst in enumerate(insts):
         check_instance(g, i, W, inst.F, inst.D, seed=1004, iters=iters, tenure=tn)
 
