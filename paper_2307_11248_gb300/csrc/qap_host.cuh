@@ -120,6 +120,7 @@ struct DevInstance {
   int64_t bound = 0;
   int64_t maxF = 0;
   int bytevec = 0;  // every difference of two F entries, and of two D entries, fits int8
+  int diff16 = 0;   // every difference of two F entries fits int16, of two D entries int8
   int wide = 0;     // outside the narrow paths: int64 elements and arithmetic
 };
 
@@ -182,6 +183,7 @@ inline qap_status inspect_instance(const int64_t* F, const int64_t* D, int n, De
   // differences of two F entries and of two D entries fit a byte (no
   // overflow here: on this branch the ranges fit int16 and int8)
   di->bytevec = !di->wide && mF <= 127 && hiF - loF <= 127 && hiD - loD <= 127;
+  di->diff16 = !di->wide && hiF - loF <= 32767 && hiD - loD <= 127;
   return QAP_OK;
 }
 
@@ -589,6 +591,7 @@ inline qapk::InstArgs inst_args(const DevInstance& d, const void* F, const void*
   I.symF = d.symF;
   I.symD = d.symD;
   I.group = group_for(d.n, nt, fbytes);
+  I.diff16 = d.diff16;
   I.F = F;
   I.Ft = d.symF ? F : Ft;
   I.D = D;

@@ -57,6 +57,7 @@ struct InstArgs {
   int n, ldF, ldP;    // ldF: elements per F row; ldP: elements per P row
   int symF, symD;
   int group;          // lanes per phase-X task (1, 2, 4 or 8)
+  int diff16;         // differences of two F entries fit int16, of two D entries int8
   const void* F;      // n x ldF (int8, int16 or int64), row-major, zero padded
   const void* Ft;     // transpose of F (== F when symF)
   const void* D;      // n x n, row-major (int8, or int64 with int64 flows)
@@ -663,10 +664,12 @@ __device__ __forceinline__ void compute_m(const WalkSmem<DT, FE>& S, int32_t* Mt
 }
 
 // Phase X of move (r, s) from Mt (pre-move): one thread per index k writes
-// the update vector of k, also by index (vw, whose a_k, c_k phase_m_update
-// reads per row) and by label (vwu at sigma[k], whose b_k, e_k it reads per
-// column): int8 flows store the packed word in both, int16 flows the int32
-// pairs (a_k, c_k) and (b_k, e_k); and, for k outside {r, s}, the recomputed
+// the update vector of k, also as the operands of phase_m_update: by index
+// the row operand (-a_k, -c_k) in vw, by label the column operand (b_k, e_k)
+// in vwu at sigma[k] (int8 flows: bytes (-a, -c, 0, 0) and the packed word
+// (b, e, a, c), one dp4a; int16 flows whose differences fit (d16): int16
+// (-a, -c) and bytes (b, e, 0, 0), one dp2a; other int16 flows: the int32
+// pairs (a, c) and (b, e)); and, for k outside {r, s}, the recomputed
 // deltas of the
 // pairs {r, k} and {s, k}, whose dot products are the entries
 //   F[r].Q[k] + F^T[r].Q^T[k] = M[r][k],  F[k].Q[s] + F^T[k].Q^T[s] = M[k][s]
@@ -676,7 +679,8 @@ __device__ __forceinline__ void compute_m(const WalkSmem<DT, FE>& S, int32_t* Mt
 template <typename DT, typename FE, int NT, bool NOTR, typename VO>
 __device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, FE>& S, const int32_t* Mt,
                                              int32_t* vw, int32_t* vwu, const int32_t* sigma,
-                                             DT* gn, int n, int ldF, int ldP, int r, int s) {
+                                             DT* gn, int n, int ldF, int ldP, int r, int s,
+                                             bool d16) {
   const FE* F = S.F;
   const FE* Ft = S.Ft;
   const int8_t* P0 = S.P;
@@ -700,8 +704,12 @@ __device__ __forceinline__ void phase_m_prep(const WalkSmem<DT, FE>& S, const in
     const typename VO::V v = VO::pack(a, b, c, e);
     VO::put(S.vec, n, k, v);
     if constexpr (sizeof(FE) == 1) {
-      vw[k] = v.x;
+      // the int8 path keeps every difference within +-127: -a, -c fit a byte
+      vw[k] = (int)(((uint32_t)(-a) & 0xffu) | (((uint32_t)(-c) & 0xffu) << 8));
       vwu[uk] = v.x;
+    } else if (d16) {
+      vw[k] = (int)(((uint32_t)(-a) & 0xffffu) | ((uint32_t)(-c) << 16));
+      vwu[uk] = (int)(((uint32_t)b & 0xffu) | (((uint32_t)e & 0xffu) << 8));
     } else {
       reinterpret_cast<int2*>(vw)[k] = make_int2(a, c);
       reinterpret_cast<int2*>(vwu)[uk] = make_int2(b, e);
@@ -754,29 +762,37 @@ __device__ __forceinline__ MShare m_share(int n, int nt) {
   return MShare{(int)threadIdx.x % gpr, (int)threadIdx.x / gpr, rows};
 }
 
-// Mt after move (r, s), in place, with the update words of phase_m_prep:
+// Mt after move (r, s), in place, with the update operands of phase_m_prep:
 //   Mt'[x][u] -= (a_x, c_x) . (b_j, e_j),  j the location of label u before
-// the move.  int8 flows: one dp4a of the bytes (a_x, c_x, 0, 0) of vw[x]
-// with vwu[u] = (b_j, e_j, a_j, c_j); int16 flows: two multiply-adds of the
-// int32 pairs.  Runs after the owner pass, which does not read Mt;
+// the move: one dp4a (int8 flows) or dp2a (int16 flows, d16) of the row
+// operand (-a_x, -c_x) with the column operand, accumulating into the entry;
+// two multiply-adds of int32 pairs for the other int16 flows.  Runs after
+// the owner pass, which does not read Mt;
 // phase_m_prep of this move read it before the barrier that precedes the
 // owner pass, and the next one reads it after the next arg-min's barrier.
 // Columns past n are padding.
 template <typename FE>
 __device__ __forceinline__ void phase_m_update(int32_t* Mt, const int32_t* vw,
-                                               const int32_t* vwu, int n, MShare sh) {
+                                               const int32_t* vwu, int n, MShare sh, bool d16) {
   if (sh.x0 >= sh.rows) return;
   const int ldm = ld_m(n);
-  if constexpr (sizeof(FE) == 1) {
+  if (sizeof(FE) == 1 || d16) {
     const int4 w = reinterpret_cast<const int4*>(vwu)[sh.g];
     for (int x = sh.x0; x < n; x += sh.rows) {
-      const int ux = (int)__byte_perm((uint32_t)vw[x], 0u, 0x4432u);
+      const int u = vw[x];
       int4* Mx = reinterpret_cast<int4*>(Mt + x * ldm) + sh.g;
       int4 m = *Mx;
-      m.x -= __dp4a(ux, w.x, 0);
-      m.y -= __dp4a(ux, w.y, 0);
-      m.z -= __dp4a(ux, w.z, 0);
-      m.w -= __dp4a(ux, w.w, 0);
+      if constexpr (sizeof(FE) == 1) {
+        m.x = __dp4a(u, w.x, m.x);
+        m.y = __dp4a(u, w.y, m.y);
+        m.z = __dp4a(u, w.z, m.z);
+        m.w = __dp4a(u, w.w, m.w);
+      } else {
+        m.x = __dp2a_lo(u, w.x, m.x);
+        m.y = __dp2a_lo(u, w.y, m.y);
+        m.z = __dp2a_lo(u, w.z, m.z);
+        m.w = __dp2a_lo(u, w.w, m.w);
+      }
       *Mx = m;
     }
   } else {
@@ -1271,7 +1287,8 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
   // by dot products over the rows of F and P.
   auto phase_x_any = [&](int r, int s) {
     if constexpr ((STORE & kProductM) != 0)
-      phase_m_prep<DT, FE, NT, kNoTr, VOsel>(S, Mt, vw, vwu, sigma, gn, n, ldF, ldP, r, s);
+      phase_m_prep<DT, FE, NT, kNoTr, VOsel>(S, Mt, vw, vwu, sigma, gn, n, ldF, ldP, r, s,
+                                              I.diff16 != 0);
     else
       phase_x<DT, FE, NT>(S, gc, gn, n, ldF, ldP, sym, G, r, s);
   };
@@ -1305,7 +1322,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         // Mt after the move (read by the next phase X, after the next
         // arg-min's barrier); after the owner pass, so that each thread's
         // candidate is ready first (asym50 10.14 -> 10.04 ms per step)
-        phase_m_update<FE>(Mt, vw, vwu, n, NT < 1024 ? msh : m_share(n, NT));
+        phase_m_update<FE>(Mt, vw, vwu, n, NT < 1024 ? msh : m_share(n, NT), I.diff16 != 0);
       }
       DT* t = gc; gc = gn; gn = t;
     }
@@ -1447,7 +1464,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         // Mt after the move (read by the next phase X, after the next
         // arg-min's barrier); after the owner pass, so that each thread's
         // candidate is ready first (asym50 10.14 -> 10.04 ms per step)
-        phase_m_update<FE>(Mt, vw, vwu, n, NT < 1024 ? msh : m_share(n, NT));
+        phase_m_update<FE>(Mt, vw, vwu, n, NT < 1024 ? msh : m_share(n, NT), I.diff16 != 0);
       }
       DT* t = gc; gc = gn; gn = t;
     }

@@ -194,3 +194,21 @@ def test_products_without_transposed_copies(n, fscale, int64):
         assert plan["products"] == 2, plan
         g = inst.search(prm)
     check_rows(g, F, D, [0, 1, 2], seed=36, iters=300, tenure=tn, descend=True)
+
+
+@pytest.mark.parametrize("n,sym,int64", [(60, False, False), (90, True, True), (130, False, True)])
+def test_products_int16_flows_with_wide_differences(n, sym, int64):
+    """int16 flows spanning more than 2^15 (differences of two entries need
+    17 bits): the products form updates M by int32 multiply-adds instead of
+    dp2a; sampled walks equal the oracle's."""
+    F, D = instances.uniform_instance(n, 1300 + n, symmetric=sym, lo=-20000, hi=20000)
+    _, D = instances.uniform_instance(n, 1400 + n, symmetric=sym)
+    np.fill_diagonal(F, 0)
+    tn = instances.periodic_tenure(n)
+    W = 2 * sms() if n <= 100 else 4
+    with q.Instance(F, D, force_int64=int64) as inst:
+        assert inst.info["flow_bytes"] == 2
+        prm = q.make_params(W, seed=37, iters=300, tenure=tn, descend=True)
+        assert inst.plan(prm)["products"] in (1, 2)
+        g = inst.search(prm)
+    check_rows(g, F, D, [0, 1, W - 1], seed=37, iters=300, tenure=tn, descend=True)
