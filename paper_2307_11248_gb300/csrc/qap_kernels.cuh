@@ -778,10 +778,7 @@ __device__ __forceinline__ void phase_m_update(int32_t* Mt, const int32_t* vw,
   const int ldm = ld_m(n);
   if (sizeof(FE) == 1 || d16) {
     const int4 w = reinterpret_cast<const int4*>(vwu)[sh.g];
-    for (int x = sh.x0; x < n; x += sh.rows) {
-      const int u = vw[x];
-      int4* Mx = reinterpret_cast<int4*>(Mt + x * ldm) + sh.g;
-      int4 m = *Mx;
+    auto upd = [&](int u, int4 m) {
       if constexpr (sizeof(FE) == 1) {
         m.x = __dp4a(u, w.x, m.x);
         m.y = __dp4a(u, w.y, m.y);
@@ -793,7 +790,25 @@ __device__ __forceinline__ void phase_m_update(int32_t* Mt, const int32_t* vw,
         m.z = __dp2a_lo(u, w.z, m.z);
         m.w = __dp2a_lo(u, w.w, m.w);
       }
-      *Mx = m;
+      return m;
+    };
+    int x = sh.x0;
+    if constexpr (sizeof(FE) == 2) {
+      // two rows per step (measured: int16 batch512 2700.6 -> 2673.8 ms per
+      // step; the int8 plans 0.3-0.4 % slower, so they keep one)
+      for (; x + sh.rows < n; x += 2 * sh.rows) {
+        const int x1 = x + sh.rows;
+        const int u0 = vw[x], u1 = vw[x1];
+        int4* M0 = reinterpret_cast<int4*>(Mt + x * ldm) + sh.g;
+        int4* M1 = reinterpret_cast<int4*>(Mt + x1 * ldm) + sh.g;
+        const int4 m0 = *M0, m1 = *M1;
+        *M0 = upd(u0, m0);
+        *M1 = upd(u1, m1);
+      }
+    }
+    for (; x < n; x += sh.rows) {
+      int4* Mx = reinterpret_cast<int4*>(Mt + x * ldm) + sh.g;
+      *Mx = upd(vw[x], *Mx);
     }
   } else {
     // (b, e) of the group's 4 labels
