@@ -1178,15 +1178,16 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         for (int i = 0; i < MAXPT; ++i)
           if (at_s(i)) nrs = -dl.get(i);
       }
-      // Rows r and s (tu): with int64 deltas or more than 8 slots their
+      // Rows r and s (tu): with int64 deltas or more than 4 slots their
       // owners take the recomputed value in this same pass, the row read
       // by those threads only (int64 batch classes 3.2 % faster; n = 100
       // grid, 256 x 24: 163.1 -> 156.6 ms, where a fused pass loading both
       // values for every slot had given 162.9 against the 180.8 of a
-      // separate rescan); with int32 deltas and at most 8 slots they
-      // recompute and rescan their segments after it (3.3 % faster at 6
-      // slots than inline).
-      constexpr bool kInlineRS = sizeof(DT) == 8 || MAXPT > 8;
+      // separate rescan; with the products form n = 50 asymmetric at 6
+      // slots 7.91 -> 7.86 ms, n = 58 at 8 slots 7.90 -> 7.72 ms); with
+      // int32 deltas and 4 slots they recompute and rescan their segments
+      // after it (n = 30: 0.4 % faster than inline).
+      constexpr bool kInlineRS = sizeof(DT) == 8 || MAXPT > 4;
       const int ubase = su == r ? 0 : n;
       const DT gu = su == r ? gr : gs;
 #pragma unroll
@@ -1218,7 +1219,7 @@ __device__ __forceinline__ void run_walk(const WalkSmem<DT, FE>& S, const InstAr
         // just applied carries its new mark
         bd = DeltaMax<DT>::v;
         bk = kNoMove;
-        // int32 deltas, at most 8 slots here: slen differs between the
+        // int32 deltas, 4 slots here: slen differs between the
         // lanes, and the slots past it are predicated off rather than left
         // by a branch (measured faster)
 #pragma unroll
