@@ -5,11 +5,14 @@
 //   shared memory   F (int8 when every difference of two F entries and of
 //                   two D entries fits a byte, else int16) and, for an
 //                   asymmetric flow, F^T; P = D[p][p] (int8) and, for
-//                   asymmetric distances, P^T; the tabu marks (int32 per
-//                   pair); the O(1)-update vectors; two recomputed delta
-//                   rows; g[k] = sum_j F[k][j]P[k][j] + F[j][k]P[j][k]
-//                   (double-buffered), or the products M of which g is the
-//                   diagonal (kProductM plans); p and the best permutation.
+//                   asymmetric distances, P^T (kNoTransposed plans keep no
+//                   transposed copies); the tabu marks (int32 per pair);
+//                   the O(1)-update vectors; two recomputed delta rows;
+//                   g[k] = sum_j F[k][j]P[k][j] + F[j][k]P[j][k] (double-
+//                   buffered), or the products M of which g is the
+//                   diagonal (kProductM plans, where P stays the walk's
+//                   starting P0 and labels sigma track the locations); p
+//                   and the best permutation.
 //   registers       the delta of every pair the thread owns: a segment of
 //                   at most MAXPT consecutive pairs (u, v) of one row u
 //                   (large-n plans keep them in a per-CTA workspace).
@@ -31,7 +34,8 @@
 //            updated delta enters the scan of the next iteration (tabu /
 //            aspiration filter, lowest (rank, r, s)).  Rows and columns r, s
 //            of P (and P^T) are then exchanged and p[r], p[s] swapped; with
-//            kProductM every thread then brings its share of M up to date.
+//            kProductM p[r], p[s] and sigma[r], sigma[s] are swapped instead
+//            and every thread brings its share of M up to date.
 //   -- barrier --  (inside the CTA arg-min: warp REDUX, then one round
 //                   through shared memory)
 // Dot products over all j count the j = x and j = k terms; removing them and

@@ -6,8 +6,8 @@ matrix-vector products of phase X with dp4a and with mma.sync (f16 inputs,
 f32 accumulation, exact for int8 values) and times both.  This test builds
 and runs it, checks that the two forms agree exactly, and prints the
 per-iteration times (run with -s to see them); it asserts nothing about
-speed.  The walk kernels use the dp4a form (or, for asymmetric int8
-instances, products maintained by a rank-2 update).
+speed.  The walk kernels use the dp4a form, or products maintained by a
+rank-2 update (int8 and int16 flows, wherever they fit shared memory).
 """
 import os
 import shutil
