@@ -227,6 +227,36 @@ void check_admission() {
     fail("big flows admitted", 2, 0, 0, {});
   if (admit(3, INT64_MIN, 1, &di) != QAP_EOVERFLOW) fail("INT64_MIN", 3, 0, 0, {});
   if (admit(257, 0, 0, &di) != QAP_EUNSUPPORTED) fail("n beyond 256", 257, 0, 0, {});
+  // the spreads that decide the byte-vector form and the products form's
+  // one-dp2a update (differences of two F entries within int16, of two D
+  // entries within int8): one entry lo, the rest hi
+  auto spread = [](int n, int64_t flo, int64_t fhi, int64_t dlo, int64_t dhi,
+                   qaph::DevInstance* di) {
+    std::vector<int64_t> F((size_t)n * n, fhi), D((size_t)n * n, dhi);
+    F[1] = flo;
+    D[1] = dlo;
+    return qaph::inspect_instance(F.data(), D.data(), n, di);
+  };
+  if (spread(20, 0, 32767, 0, 127, &di) != QAP_OK || di.wide || di.bytevec || !di.diff16)
+    fail("F spread 2^15 - 1", 20, 0, 0, {});
+  if (spread(20, -1, 32767, 0, 127, &di) != QAP_OK || di.wide || di.diff16)
+    fail("F spread 2^15", 20, 0, 0, {});
+  if (spread(20, 0, 99, -1, 127, &di) != QAP_OK || di.wide || di.bytevec || di.diff16)
+    fail("D spread 128", 20, 0, 0, {});
+  if (spread(20, -27, 100, 0, 127, &di) != QAP_OK || !di.bytevec || !di.diff16)
+    fail("byte vectors", 20, 0, 0, {});
+}
+
+// The search parameters' phase X form: AUTO or DOTS, nothing else.
+void check_params() {
+  qap_search_params p{};
+  p.starts = 1;
+  for (int form : {-1, 0, 1, 2}) {
+    p.phase_x = form;
+    const bool ok = qaph::validate_params(&p) == QAP_OK;
+    if (ok != (form == QAP_PHASE_X_AUTO || form == QAP_PHASE_X_DOTS))
+      fail("phase_x validation", form, 0, 0, {});
+  }
 }
 
 int main() {
@@ -235,6 +265,7 @@ int main() {
     return 1;
   }
   check_admission();
+  check_params();
   check_choose_plan();
   check_choose_plan_fit();
   if (fails) {
