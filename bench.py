@@ -385,6 +385,7 @@ def measure_asym50(args, q, stream, flush, dev, world, rank, khash, baselines=Tr
         "config": {"workload": f"asym50: tabu n=50 asym uniform[0,99], {W} walks x {iters} iters",
                    "n": n, "walks_per_gpu": W, "iters": iters, "tenure": list(w["tenure"]),
                    "aspiration": True, "launch": "persistent, one launch per step",
+                   "phase_x": args.phase_x, "products": int(plan["products"]),
                    "threads_per_walk": plan["threads_per_walk"],
                    "pairs_per_thread": plan["pairs_per_thread"], "grid": plan["grid"],
                    "l2": "flushed between timed steps (256 MiB write); working set on chip"},
@@ -490,10 +491,10 @@ def measure_grid100(args, q, stream, flush, dev, world, rank, khash, baselines=T
         "tabu_iters_per_s": float(outs["iters_done"].sum().item()) * world /
         (max_ms / 1e3 / args.steps),
         "config": {"workload": f"grid100: 2opt then tabu, n=100 grid, {W} walks x {iters} iters",
-                   "launch": "persistent, replayed as one CUDA graph",
+                   "launch": "persistent, replayed as one CUDA graph", "phase_x": args.phase_x,
                    "threads_per_walk": plan["threads_per_walk"],
                    "pairs_per_thread": plan["pairs_per_thread"], "grid": plan["grid"],
-                   "ctas_per_sm": plan["ctas_per_sm"],
+                   "ctas_per_sm": plan["ctas_per_sm"], "products": int(plan["products"]),
                    "evals": "2opt moves and tabu iterations, n(n-1)/2 each",
                    "l2": "flushed between timed steps"},
         "roofline": roof, "issue": issue, "gpu_launches": args.steps, "clocks": clock_fields(clk),
@@ -586,7 +587,7 @@ def measure_batch512(args, q, stream, flush, dev, world, rank, khash, baselines=
         ach = cls_bytes[i] / (class_ms[i] / 1e3) / 1e9 if class_ms[i] > 0 else None
         return {"n": [c["nmin"], c["nmax"]], "instances": c["instances"], "walks": c["walks"],
                 "plan": [c["threads_per_walk"], c["pairs_per_thread"]],
-                "products": bool(c["products"]), "workspace": bool(c["workspace"]),
+                "products": int(c["products"]), "workspace": bool(c["workspace"]),
                 "grid": c["grid"], "ctas_per_sm": c["ctas_per_sm"],
                 "kernel_ms": round(float(class_ms[i]), 3),
                 "share_of_step": round(float(class_ms[i]) / (step_s * 1e3), 4),
@@ -611,11 +612,12 @@ def measure_batch512(args, q, stream, flush, dev, world, rank, khash, baselines=
                    "launch": "one persistent launch per size class, classes concurrent on "
                              "forked streams, device work queues, largest n first",
                    "classes": nc, "tenure": "[0.9n, 1.1n] redrawn every 2n",
+                   "phase_x": args.phase_x,
                    "autotune_s": round(tune_s, 2),
                    "autotuned": [{"n": [r["nmin"], r["nmax"]],
                                   "plan": [r["threads_per_walk"], r["pairs_per_thread"]],
                                   "workspace": bool(r["workspace"]),
-                                  "products": bool(r["products"]),
+                                  "products": int(r["products"]),
                                   "trial_ms": round(r["trial_ms"], 3),
                                   "rule_ms": round(r["rule_ms"], 3)} for r in tune],
                    "l2": "flushed between timed steps (256 MiB write)"},
