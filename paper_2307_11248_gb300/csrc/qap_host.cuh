@@ -268,20 +268,19 @@ inline bool has_notrans_form(const Plan& p, int fbytes) {
   return has_product_form(p, fbytes) && p.maxpt >= 12 && (p.nt == 256 || p.nt == 512);
 }
 
-// The products form of a register plan when the flows are stored as int8 or
-// int16 and M fits shared memory too (phase X then reads M instead of
-// computing dot products), unless the caller asks for the dot products.  Measured with
-// 2 walks per SM, 4000 iterations: asymmetric n = 60 / 70 / 80 8.4 / 10.4 /
-// 12.9 ms against 10.3 / 11.0 / 13.4 for symmetric ones by dot products;
-// symmetric n = 50 / 60 / 70 / 80 by products 6.7 / 8.4 / 10.3 / 12.7 ms;
-// n = 100 at 512 x 12 symmetric 10.2 against 12.1 ms.  At 24 slots (not
-// compiled with M) the n = 100 grid took 157.8 against 154.2 ms.
 // The form a plan reports: 0 dot products, 1 maintained products, 2 the
 // same without the transposed copies of F and P.
 inline int products_form(const Plan& p) {
   return !(p.store & qapk::kProductM) ? 0 : (p.store & qapk::kNoTransposed) ? 2 : 1;
 }
 
+// The products form of a register plan when the flows are stored as int8 or
+// int16 and M fits shared memory too (phase X then reads M instead of
+// computing dot products), unless the caller asks for the dot products.
+// Measured with 2 walks per SM, 4000 iterations: asymmetric n = 60 / 70 /
+// 80 8.4 / 10.4 / 12.9 ms against 10.3 / 11.0 / 13.4 for symmetric ones by
+// dot products; symmetric n = 50 / 60 / 70 / 80 by products 6.7 / 8.4 /
+// 10.3 / 12.7 ms; n = 100 at 512 x 12 symmetric 10.2 against 12.1 ms.
 // Where M does not fit beside the transposed copies (or would keep two
 // walks from sharing an SM where the plan was taken for that), the form
 // without the copies.  `fits` says whether a plan fits.
